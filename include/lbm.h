@@ -1,0 +1,215 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) reactive two-component lattice
+ * Boltzmann library: capillary infiltration of a wetting melt with surface
+ * reaction, precipitation and solid growth (Sergi, Grossi, Leidi, Ortona,
+ * "Lattice Boltzmann simulation of the surface growth effects for the
+ * infiltration of molten Si in carbon preforms", arXiv:1309.6726).
+ *
+ * One handle holds one lattice or a batch of independent lattices
+ * ("capillaries") of uneven size; every call below acts on all of them.
+ * The time step it runs is the paper's Sec. II model, per node and step:
+ *
+ *   streaming of the two D2Q9 populations and the D2Q4 solute with
+ *   half-way bounce-back at the solid ("bounce-back rule", Sec. II);
+ *   densities and momenta;
+ *   Martys-Chen cohesive (A-B) and adhesive (fluid-solid) forces,
+ *     F_s = -G_c rho_s(x) sum_i w_i rho_s'(x+e_i) e_i
+ *           - G_ads,s rho_s(x) sum_i w_i solid(x+e_i) e_i,
+ *     G_ads,A = -g_ads, G_ads,B = +g_ads ("cohesive ... adhesive forces",
+ *     Sec. II; g_ads sets the 30 degree contact angle of Sec. I);
+ *   Shan-Chen velocity shift and BGK collision of each component;
+ *   BGK collision of the D2Q4 solute advected by the barycentric velocity
+ *     ("weak coupling with fluid flow", Sec. II), with the inlet column
+ *     x = 0 imposing concentration c_in when enabled;
+ *   first-order surface reaction k_r at fluid nodes where A is the
+ *     majority and that touch the solid: the consumed solute precipitates
+ *     ("mass deposits on the surface", Sec. II);
+ *   growth: a node whose precipitated mass reaches m_threshold turns solid
+ *     ("when the cumulated mass exceeds a threshold value, the solid phase
+ *     expands", Sec. II); its fluid, solute and deposit go to a per-lattice
+ *     ledger so that mass is accounted exactly.
+ * Lattices are periodic in x and y; node (x, y) is row y, column x.
+ *
+ * Threading and streams: a handle is not thread-safe.  Calls that only
+ * launch work (lbm_step) are asynchronous on the handle's stream (its own
+ * non-blocking stream unless lbm_set_stream bound another); every call
+ * that returns data to the host synchronizes that stream first.
+ *
+ * Errors: every call returns an lbm_status; on failure the handle keeps a
+ * message that lbm_last_error returns.  Nothing throws across the ABI.  A
+ * CUDA error leaves the handle unusable (LBM_ECUDA from then on).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,   /* bad argument (sizes, NULL, out-of-range index) */
+    LBM_ENOMEM = 2,   /* device or host allocation failed */
+    LBM_ECUDA = 3,    /* a CUDA call or kernel failed; handle is dead */
+    LBM_ETIMEOUT = 4, /* a bounded device wait ran out */
+    LBM_ENAN = 5,     /* non-finite density seen in some lattice */
+    LBM_EIO = 6       /* checkpoint file could not be read or written */
+} lbm_status;
+
+/* Storage of the populations between steps.  Arithmetic is FP32 in both;
+ * the deposit and the growth test are FP64 in both. */
+typedef enum {
+    LBM_FP32 = 0, /* populations stored as FP32 */
+    LBM_FP16 = 1  /* populations stored as FP16 deviations from the lattice
+                     weight times the node's own density, that density
+                     rounded to FP16 and kept in a moment plane */
+} lbm_precision;
+
+/* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,
+ * read once at create (the caller keeps ownership).  Every fluid node
+ * starts at rest equilibrium for its rho_a, rho_b and conc; values at solid
+ * nodes are ignored.  [cap_x0, cap_x1) is the capillary section the
+ * observables of Sec. III (front, radii, Delta e, closure) are taken over;
+ * walls are expected at rows 0 and ny-1 there. */
+typedef struct lbm_geometry {
+    int32_t nx, ny;        /* nx >= 1, ny >= 3 */
+    const uint8_t *solid;  /* 1 = solid, 0 = fluid */
+    const float *rho_a;    /* initial density of component A (wetting) */
+    const float *rho_b;    /* initial density of component B */
+    const float *conc;     /* initial solute concentration */
+    int32_t cap_x0, cap_x1;/* 0 <= cap_x0 < cap_x1 <= nx */
+} lbm_geometry;
+
+/* Model constants of one lattice (lattice units). */
+typedef struct lbm_params {
+    double tau_a, tau_b;  /* BGK relaxation times of A and B, > 1/2 */
+    double tau_d;         /* solute relaxation time, D = (tau_d - 1/2)/2 */
+    double g_coh;         /* cohesion strength G_c */
+    double g_ads;         /* adhesion strength g (A attracted for g > 0) */
+    double k_r;           /* reaction-rate constant [lu/ts], >= 0 */
+    double m_threshold;   /* precipitated mass that turns a node solid */
+    double c_in;          /* concentration imposed at the inlet column */
+    double body_force_x;  /* uniform acceleration along x (checks only) */
+    int32_t inlet;        /* 1: column x = 0 imposes c_in */
+    int32_t precision;    /* lbm_precision; must be equal over a batch */
+} lbm_params;
+
+/* Observables of one lattice at the current step (paper Sec. III).
+ * front: centerline position of the A/B front past the capillary
+ *   entrance (Fig. 2, Eq. 1), linear interpolation of rho_A - rho_B on the
+ *   centerline row(s), NaN if there is none;
+ * wetted_lower / wetted_upper: fluid nodes along each wall profile in the
+ *   section where A is the majority;
+ * r_min, r_ave: minimum and mean half-aperture; r_h: fluid area between
+ *   the lower-wall profile and the centerline over that profile's length
+ *   (Fig. 4); delta_e: largest grown wall thickness, H/2 for a closed
+ *   column (Fig. 3);
+ * precip_mass: all mass precipitated so far; mass_a/b/c: A, B and solute
+ *   in the fluid; ledger_*: what growth moved out of the fluid;
+ * closed: some section column is entirely solid; closure_step: the first
+ *   step count at which that happened (-1 if never); nonfinite: a
+ *   non-finite density was seen. */
+typedef struct lbm_obs {
+    int64_t step;
+    double front;
+    double wetted_lower, wetted_upper;
+    double r_min, r_h, r_ave;
+    double delta_e;
+    double precip_mass;
+    double mass_a, mass_b, mass_c;
+    double ledger_a, ledger_b, ledger_c, ledger_m;
+    int32_t closed;
+    int32_t nonfinite;
+    int64_t closure_step;
+} lbm_obs;
+
+/* Field selectors for lbm_get_fields / lbm_set_fields.  Populations are
+ * the post-streaming state at the current step, FP32, direction-major:
+ *   LBM_FIELD_POPS: 22 planes of ny*nx floats: A (9, D2Q9 order below),
+ *                   B (9), solute (4);
+ *   LBM_FIELD_DEPOSIT: ny*nx doubles;
+ *   LBM_FIELD_DENSITY: 3 planes of ny*nx floats: rho_A, rho_B, C.
+ * D2Q9 order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1);
+ * D2Q4 order: (1,0) (0,1) (-1,0) (0,-1).  Solid nodes read as zero. */
+enum {
+    LBM_FIELD_POPS = 0,
+    LBM_FIELD_DEPOSIT = 1,
+    LBM_FIELD_DENSITY = 2
+};
+
+typedef struct lbm_handle lbm_handle;
+
+/* Creates a handle holding one lattice.  Copies the geometry to the device
+ * (host->device once) and allocates everything the steps need; *out is
+ * NULL on failure.  Returns EINVAL for bad sizes or parameters, ENOMEM,
+ * ECUDA. */
+lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p,
+                      lbm_handle **out);
+
+/* Same for `count` independent lattices (g[k], p[k]) advanced together by
+ * one launch per step over a packed ragged layout. */
+lbm_status lbm_create_batch(const lbm_geometry *g, const lbm_params *p,
+                            int32_t count, lbm_handle **out);
+
+/* Binds a CUDA stream (a cudaStream_t passed as void*; NULL = the handle's
+ * own stream).  The caller keeps the stream alive while bound. */
+lbm_status lbm_set_stream(lbm_handle *h, void *cuda_stream);
+
+/* Advances every lattice by n >= 0 steps (asynchronous). */
+lbm_status lbm_step(lbm_handle *h, int64_t n);
+
+/* Number of completed steps. */
+int64_t lbm_step_count(const lbm_handle *h);
+
+/* Number of lattices in the handle. */
+int32_t lbm_count(const lbm_handle *h);
+
+/* Observables of every lattice: out[count].  Synchronizes.  Returns
+ * LBM_ENAN (after filling out) if some lattice holds a non-finite value. */
+lbm_status lbm_observables(lbm_handle *h, lbm_obs *out);
+
+/* Current solid mask of lattice k: n must be ny*nx bytes. */
+lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k, uint8_t *host,
+                              size_t n);
+
+/* Copies a field of lattice k (see LBM_FIELD_*) to host memory of exactly
+ * `bytes` bytes.  Synchronizes. */
+lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
+                          void *host, size_t bytes);
+
+/* Replaces the post-streaming populations (LBM_FIELD_POPS) or the deposit
+ * (LBM_FIELD_DEPOSIT) of lattice k.  Values at solid nodes are ignored. */
+lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
+                          const void *host, size_t bytes);
+
+/* Writes / reads the complete device state (populations in their stored
+ * precision, mask, deposit, ledgers, counters, step) to / from a file; a
+ * loaded handle continues bit for bit as the saved one would have.  The
+ * handle given to lbm_load must have been created with the same
+ * geometry sizes and parameters. */
+lbm_status lbm_save(lbm_handle *h, const char *path);
+lbm_status lbm_load(lbm_handle *h, const char *path);
+
+/* Frees everything; NULL is allowed. */
+void lbm_destroy(lbm_handle *h);
+
+/* Message of the last failure on h (or of the last failed create when h is
+ * NULL); never NULL. */
+const char *lbm_last_error(const lbm_handle *h);
+
+/* Effective radius (paper Sec. III, Fig. 4): Eq. 1's late-time speed
+ * v = gamma H cos(theta) / (6 mu L) solved for H with v the least-squares
+ * slope of the front history z(t) (n >= 2 samples), r_eff = H / 2.
+ * Host-only arithmetic. */
+lbm_status lbm_fit_reff(const double *t, const double *z, int32_t n,
+                        double gamma, double mu, double length,
+                        double cos_theta0, double *r_eff);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,769 @@
+// lbm_api.cu -- the C ABI declared in include/lbm.h: handle life cycle,
+// packed ragged layout of a batch, stepping, observables, field access,
+// checkpoints.  All arithmetic of the method runs in the kernels of
+// lbm_step.cu and lbm_aux.cu; this file only sizes, allocates, copies and
+// launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbmk {
+cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
+                               int ty, bool half, cudaStream_t s);
+cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
+                            const CUtensorMap *mom_maps, int ntiles, int tx,
+                            int ty, bool half, int *err, cudaStream_t s);
+int tma_box_x(int tx, bool half);
+__global__ void k_rest_state(const LatDesc *, int, const float *,
+                             const float *, const float *, const uint8_t *,
+                             float *);
+__global__ void k_unstream(const LatDesc *, int, const float *,
+                           const uint8_t *, uint8_t, void *, __half *, bool);
+__global__ void k_export(const LatDesc *, int, const void *, const __half *,
+                         const uint8_t *, const double *, long long, bool,
+                         float *, float *, double *);
+__global__ void k_settle(const LatDesc *, int, const void *, const __half *,
+                         uint8_t *, double *, LatState *, long long, bool);
+__global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
+__global__ void k_obs_columns(const LatDesc *, const int32_t *,
+                              const int64_t *, int, const void *,
+                              const __half *, const uint8_t *,
+                              const double *, long long, bool, ColObs *);
+struct LbmObsDev;
+__global__ void k_obs_reduce(const LatDesc *, const int64_t *,
+                             const ColObs *, const int16_t *,
+                             const LatState *, long long, LbmObsDev *);
+}  // namespace lbmk
+
+using namespace lbmk;
+
+static_assert(sizeof(lbm_obs) == 8 * 16 + 4 * 2 + 8, "lbm_obs layout");
+
+struct lbm_handle {
+    int count = 0;
+    bool half = false;
+    int tx = 32, ty = 8;
+    bool use_tma = true;
+    std::vector<LatDesc> desc;
+    std::vector<int64_t> col_base;   // first column of lattice l (all columns)
+    int64_t ncols = 0;               // columns of all lattices
+    int64_t nsec = 0;                // section columns of all lattices
+    int ntiles = 0;
+    int64_t pop_elems = 0, mom_elems = 0, node_elems = 0;
+    size_t max_nodes = 0;            // largest nx*ny
+    // device
+    LatDesc *d_desc = nullptr;
+    int32_t *d_tile_lat = nullptr;
+    int32_t *d_col_lat = nullptr;
+    int64_t *d_col_base = nullptr;
+    void *d_pop[2] = {nullptr, nullptr};
+    __half *d_mom[2] = {nullptr, nullptr};
+    uint8_t *d_mask = nullptr;
+    double *d_m = nullptr;
+    int32_t *d_col_fluid = nullptr;
+    int16_t *d_wall0 = nullptr;
+    LatState *d_st = nullptr;
+    int64_t *d_step = nullptr;
+    unsigned int *d_done = nullptr;
+    ColObs *d_cols = nullptr;
+    void *d_obs = nullptr;
+    float *d_canon = nullptr;      // [22][ny][nx] scratch of one lattice
+    float *d_dens = nullptr;       // [3][ny][nx]
+    double *d_dep = nullptr;       // [ny][nx]
+    CUtensorMap *d_maps = nullptr;     // [2 buffers][count] population maps
+    CUtensorMap *d_mom_maps = nullptr; // [2 buffers][count] FP16 moment maps
+    int *d_err = nullptr;              // kernel error flags
+    int cur = 0;
+    int64_t steps = 0;
+    cudaStream_t own = nullptr, stream = nullptr;
+    bool dead = false;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static lbm_status fail(lbm_handle *h, lbm_status st, const std::string &msg) {
+    if (h) {
+        h->err = msg;
+        if (st == LBM_ECUDA) h->dead = true;
+    } else {
+        g_create_err = msg;
+    }
+    return st;
+}
+
+#define CK(h, call)                                                        \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess)                                             \
+            return fail((h), LBM_ECUDA,                                    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+static void free_all(lbm_handle *h) {
+    void *ps[] = {h->d_desc, h->d_tile_lat, h->d_col_lat, h->d_col_base,
+                  h->d_pop[0], h->d_pop[1], h->d_mom[0], h->d_mom[1],
+                  h->d_mask, h->d_m, h->d_col_fluid, h->d_wall0, h->d_st,
+                  h->d_step, h->d_done, h->d_cols, h->d_obs, h->d_canon,
+                  h->d_dens, h->d_dep, h->d_maps, h->d_mom_maps, h->d_err};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    if (h->own) cudaStreamDestroy(h->own);
+}
+
+static bool valid_params(const lbm_params &p, std::string &why) {
+    if (!(p.tau_a > 0.5 && p.tau_b > 0.5 && p.tau_d > 0.5)) {
+        why = "relaxation times must exceed 1/2";
+        return false;
+    }
+    if (!(p.k_r >= 0.0) || !std::isfinite(p.k_r)) {
+        why = "k_r must be finite and >= 0";
+        return false;
+    }
+    if (!std::isfinite(p.g_coh) || !std::isfinite(p.g_ads) ||
+        !std::isfinite(p.c_in) || !std::isfinite(p.body_force_x) ||
+        std::isnan(p.m_threshold)) {
+        why = "non-finite constant";
+        return false;
+    }
+    if (p.precision != LBM_FP32 && p.precision != LBM_FP16) {
+        why = "unknown precision";
+        return false;
+    }
+    return true;
+}
+
+static void pick_tile(lbm_handle *h) {
+    const char *e = getenv("LBM_TILE");
+    if (e) {
+        int a = 0, b = 0;
+        if (sscanf(e, "%dx%d", &a, &b) == 2) {
+            h->tx = a;
+            h->ty = b;
+        }
+    }
+    const char *k = getenv("LBM_KERNEL");
+    if (k && strcmp(k, "direct") == 0) h->use_tma = false;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// One 3-D tensor map per lattice and buffer: (x, y, plane) over the lattice
+// (x < nx, y < ny: coordinates beyond read as zeros), box = the kernel's
+// tile plus halo, all planes.
+static bool make_maps(lbm_handle *h, std::string &why) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        why = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    const int count = h->count;
+    const size_t esz = h->half ? 2 : 4;
+    std::vector<CUtensorMap> maps(2 * count), moms(2 * count);
+    for (int b = 0; b < 2; ++b) {
+        for (int l = 0; l < count; ++l) {
+            const LatDesc &d = h->desc[l];
+            cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NPOP};
+            cuuint64_t strides[2] = {(cuuint64_t)d.pitch * esz, (cuuint64_t)d.plane * esz};
+            cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx, h->half),
+                                 (cuuint32_t)(h->ty + 4), (cuuint32_t)NPOP};
+            cuuint32_t es[3] = {1, 1, 1};
+            void *base = (char *)h->d_pop[b] + (size_t)d.pop_off * esz;
+            CUresult r = enc(&maps[b * count + l],
+                             h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                             3, base, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                why = "cuTensorMapEncodeTiled failed for populations, code " +
+                      std::to_string((int)r);
+                return false;
+            }
+            if (h->half) {
+                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NMOM};
+                cuuint32_t mbox[3] = {box[0], box[1], (cuuint32_t)NMOM};
+                void *mbase = (char *)h->d_mom[b] + (size_t)d.mom_off * 2;
+                r = enc(&moms[b * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                        mbase, mdims, strides, mbox, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    why = "cuTensorMapEncodeTiled failed for moments, code " +
+                          std::to_string((int)r);
+                    return false;
+                }
+            }
+        }
+    }
+    if (cudaMalloc(&h->d_maps, maps.size() * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMemcpy(h->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        why = "tensor map upload";
+        return false;
+    }
+    if (h->half &&
+        (cudaMalloc(&h->d_mom_maps, moms.size() * sizeof(CUtensorMap)) != cudaSuccess ||
+         cudaMemcpy(h->d_mom_maps, moms.data(), moms.size() * sizeof(CUtensorMap),
+                    cudaMemcpyHostToDevice) != cudaSuccess)) {
+        why = "tensor map upload";
+        return false;
+    }
+    return true;
+}
+
+extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
+                                       const lbm_params *p, int32_t count,
+                                       lbm_handle **out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !p || count < 1)
+        return fail(nullptr, LBM_EINVAL, "geometry/params NULL or count < 1");
+    std::string why;
+    for (int l = 0; l < count; ++l) {
+        const lbm_geometry &G = g[l];
+        if (G.nx < 1 || G.ny < 3 || !G.solid || !G.rho_a || !G.rho_b ||
+            !G.conc)
+            return fail(nullptr, LBM_EINVAL,
+                        "lattice " + std::to_string(l) +
+                            ": need nx >= 1, ny >= 3 and all arrays");
+        if ((int64_t)G.nx * G.ny > (int64_t)1 << 31)
+            return fail(nullptr, LBM_EINVAL, "lattice too large");
+        if (!(0 <= G.cap_x0 && G.cap_x0 < G.cap_x1 && G.cap_x1 <= G.nx))
+            return fail(nullptr, LBM_EINVAL,
+                        "lattice " + std::to_string(l) + ": bad section");
+        if (!valid_params(p[l], why))
+            return fail(nullptr, LBM_EINVAL,
+                        "lattice " + std::to_string(l) + ": " + why);
+        if (p[l].precision != p[0].precision)
+            return fail(nullptr, LBM_EINVAL, "mixed precision in a batch");
+    }
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation");
+    h->count = count;
+    h->half = p[0].precision == LBM_FP16;
+    pick_tile(h);
+
+    // ---- packed ragged layout ------------------------------------------
+    h->desc.resize(count);
+    h->col_base.resize(count);
+    int64_t pop = 0, mom = 0, node = 0, cols = 0, sec = 0;
+    int tiles = 0;
+    for (int l = 0; l < count; ++l) {
+        const lbm_geometry &G = g[l];
+        const lbm_params &P = p[l];
+        LatDesc &d = h->desc[l];
+        d.nx = G.nx;
+        d.ny = G.ny;
+        d.pitch = (G.nx + 31) / 32 * 32;
+        d.tiles_x = (G.nx + h->tx - 1) / h->tx;
+        d.tile_base = tiles;
+        tiles += d.tiles_x * ((G.ny + h->ty - 1) / h->ty);
+        d.cap_x0 = G.cap_x0;
+        d.cap_x1 = G.cap_x1;
+        d.inlet = P.inlet ? 1 : 0;
+        d.plane = (int64_t)d.ny * d.pitch;
+        d.node_off = node;
+        d.pop_off = pop;
+        d.mom_off = mom;
+        d.col_off = sec;
+        node += d.plane;
+        pop += NPOP * d.plane;
+        mom += NMOM * d.plane;
+        h->col_base[l] = cols;
+        cols += d.nx;
+        sec += G.cap_x1 - G.cap_x0;
+        d.tau_a = (float)P.tau_a;
+        d.tau_b = (float)P.tau_b;
+        d.inv_tau_a = (float)(1.0 / P.tau_a);
+        d.inv_tau_b = (float)(1.0 / P.tau_b);
+        d.inv_tau_d = (float)(1.0 / P.tau_d);
+        d.g_coh = (float)P.g_coh;
+        d.g_ads = (float)P.g_ads;
+        d.k_r = (float)P.k_r;
+        d.c_in = (float)P.c_in;
+        d.body_x = (float)P.body_force_x;
+        d.m_th = P.m_threshold;
+        h->max_nodes = std::max(h->max_nodes, (size_t)G.nx * G.ny);
+    }
+    h->ntiles = tiles;
+    h->pop_elems = pop;
+    h->mom_elems = mom;
+    h->node_elems = node;
+    h->ncols = cols;
+    h->nsec = sec;
+
+    std::vector<int32_t> tile_lat(tiles), col_lat(cols);
+    std::vector<int32_t> col_fluid(sec);
+    std::vector<int16_t> wall0(2 * sec);
+    std::vector<uint8_t> mask(node, 0);
+    for (int l = 0; l < count; ++l) {
+        const LatDesc &d = h->desc[l];
+        const int nt = d.tiles_x * ((d.ny + h->ty - 1) / h->ty);
+        for (int k = 0; k < nt; ++k) tile_lat[d.tile_base + k] = l;
+        for (int x = 0; x < d.nx; ++x) col_lat[h->col_base[l] + x] = l;
+        const uint8_t *S = g[l].solid;
+        for (int y = 0; y < d.ny; ++y)
+            for (int x = 0; x < d.nx; ++x)
+                mask[d.node_off + (int64_t)y * d.pitch + x] =
+                    S[(int64_t)y * d.nx + x] ? 7 : 0;
+        for (int x = d.cap_x0; x < d.cap_x1; ++x) {
+            int fl = 0, b = 0, t = 0;
+            for (int y = 0; y < d.ny; ++y) fl += S[(int64_t)y * d.nx + x] == 0;
+            while (b < d.ny && S[(int64_t)b * d.nx + x]) ++b;
+            while (t < d.ny && S[(int64_t)(d.ny - 1 - t) * d.nx + x]) ++t;
+            const int64_t k = d.col_off + (x - d.cap_x0);
+            col_fluid[k] = fl;
+            wall0[2 * k] = (int16_t)std::min(b, 32767);
+            wall0[2 * k + 1] = (int16_t)std::min(t, 32767);
+        }
+    }
+
+    // ---- device allocations ----------------------------------------------
+    const size_t esz = h->half ? sizeof(__half) : sizeof(float);
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, n)                                                      \
+    if (e == cudaSuccess) e = dalloc(&(ptr), (n));
+    AL(h->d_desc, count);
+    AL(h->d_tile_lat, tiles);
+    AL(h->d_col_lat, cols);
+    AL(h->d_col_base, count);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[0], pop * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[1], pop * esz);
+    if (h->half) {
+        AL(h->d_mom[0], mom);
+        AL(h->d_mom[1], mom);
+    }
+    AL(h->d_mask, node);
+    AL(h->d_m, node);
+    AL(h->d_col_fluid, sec);
+    AL(h->d_wall0, 2 * sec);
+    AL(h->d_st, count);
+    AL(h->d_step, 1);
+    AL(h->d_done, 1);
+    AL(h->d_cols, cols);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_obs, count * sizeof(lbm_obs));
+    AL(h->d_canon, NPOP * h->max_nodes);
+    AL(h->d_dens, 3 * h->max_nodes);
+    AL(h->d_dep, h->max_nodes);
+    AL(h->d_err, 1);
+#undef AL
+    if (e != cudaSuccess) {
+        std::string msg = std::string("device allocation: ") + cudaGetErrorString(e);
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, msg);
+    }
+    lbm_status st = LBM_OK;
+    auto bad = [&](cudaError_t ce, const char *what) {
+        if (ce != cudaSuccess && st == LBM_OK) {
+            g_create_err = std::string(what) + ": " + cudaGetErrorString(ce);
+            st = LBM_ECUDA;
+        }
+    };
+    bad(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking), "stream");
+    h->stream = h->own;
+    cudaStream_t s = h->stream;
+    bad(cudaMemcpy(h->d_desc, h->desc.data(), count * sizeof(LatDesc), cudaMemcpyHostToDevice), "desc");
+    bad(cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
+    bad(cudaMemcpy(h->d_col_lat, col_lat.data(), cols * sizeof(int32_t), cudaMemcpyHostToDevice), "cols");
+    bad(cudaMemcpy(h->d_col_base, h->col_base.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice), "colbase");
+    bad(cudaMemcpy(h->d_mask, mask.data(), node, cudaMemcpyHostToDevice), "mask");
+    bad(cudaMemcpy(h->d_col_fluid, col_fluid.data(), sec * sizeof(int32_t), cudaMemcpyHostToDevice), "colfluid");
+    bad(cudaMemcpy(h->d_wall0, wall0.data(), 2 * sec * sizeof(int16_t), cudaMemcpyHostToDevice), "wall0");
+    bad(cudaMemset(h->d_pop[0], 0, pop * esz), "memset");
+    bad(cudaMemset(h->d_pop[1], 0, pop * esz), "memset");
+    if (h->half) {
+        bad(cudaMemset(h->d_mom[0], 0, mom * sizeof(__half)), "memset");
+        bad(cudaMemset(h->d_mom[1], 0, mom * sizeof(__half)), "memset");
+    }
+    bad(cudaMemset(h->d_m, 0, node * sizeof(double)), "memset");
+    std::vector<LatState> st0(count);
+    for (auto &x : st0) {
+        memset(&x, 0, sizeof(x));
+        x.closure = ~0ull;
+    }
+    bad(cudaMemcpy(h->d_st, st0.data(), count * sizeof(LatState), cudaMemcpyHostToDevice), "state");
+    bad(cudaMemset(h->d_step, 0, sizeof(int64_t)), "memset");
+    bad(cudaMemset(h->d_err, 0, sizeof(int)), "memset");
+    if (st == LBM_OK && h->use_tma) {
+        std::string why;
+        if (!make_maps(h, why)) {
+            g_create_err = why;
+            st = LBM_ECUDA;
+        }
+    }
+    bad(cudaMemset(h->d_done, 0, sizeof(unsigned)), "memset");
+    // initial rest state of every lattice through the unstream path
+    float *tmp = nullptr;
+    uint8_t *tsol = nullptr;
+    if (st == LBM_OK) {
+        bad(dalloc(&tmp, 3 * h->max_nodes), "alloc");
+        bad(dalloc(&tsol, h->max_nodes), "alloc");
+    }
+    for (int l = 0; l < count && st == LBM_OK; ++l) {
+        const LatDesc &d = h->desc[l];
+        const size_t N = (size_t)d.nx * d.ny;
+        bad(cudaMemcpy(tmp, g[l].rho_a, N * 4, cudaMemcpyHostToDevice), "rho_a");
+        bad(cudaMemcpy(tmp + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice), "rho_b");
+        bad(cudaMemcpy(tmp + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice), "conc");
+        bad(cudaMemcpy(tsol, g[l].solid, N, cudaMemcpyHostToDevice), "solid");
+        dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
+        k_rest_state<<<grid, blk, 0, s>>>(h->d_desc, l, tmp, tmp + N, tmp + 2 * N, tsol, h->d_canon);
+        k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->d_mom[0], h->half);
+        bad(cudaGetLastError(), "init kernels");
+        bad(cudaStreamSynchronize(s), "init sync");
+    }
+    if (tmp) cudaFree(tmp);
+    if (tsol) cudaFree(tsol);
+    if (st != LBM_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p,
+                                 lbm_handle **out) {
+    return lbm_create_batch(g, p, 1, out);
+}
+
+extern "C" void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+extern "C" const char *lbm_last_error(const lbm_handle *h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+extern "C" int64_t lbm_step_count(const lbm_handle *h) { return h ? h->steps : -1; }
+extern "C" int32_t lbm_count(const lbm_handle *h) { return h ? h->count : 0; }
+
+extern "C" lbm_status lbm_set_stream(lbm_handle *h, void *cuda_stream) {
+    if (!h) return LBM_EINVAL;
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own;
+    return LBM_OK;
+}
+
+static StepArgs step_args(lbm_handle *h) {
+    StepArgs a;
+    a.desc = h->d_desc;
+    a.tile_lat = h->d_tile_lat;
+    a.fin = h->d_pop[h->cur];
+    a.fout = h->d_pop[h->cur ^ 1];
+    a.min_ = h->d_mom[h->cur];
+    a.mout = h->d_mom[h->cur ^ 1];
+    a.mask = h->d_mask;
+    a.m = h->d_m;
+    a.col_fluid = h->d_col_fluid;
+    a.st = h->d_st;
+    a.step = h->d_step;
+    a.done = h->d_done;
+    return a;
+}
+
+extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
+    if (!h || n < 0) return fail(h, LBM_EINVAL, "bad handle or n < 0");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    for (int64_t k = 0; k < n; ++k) {
+        StepArgs a = step_args(h);
+        cudaError_t e =
+            h->use_tma
+                ? launch_step_tma(a, h->d_maps + h->cur * h->count,
+                                  h->half ? h->d_mom_maps + h->cur * h->count : nullptr,
+                                  h->ntiles, h->tx, h->ty, h->half, h->d_err, h->stream)
+                : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
+        if (e == cudaErrorInvalidValue && k == 0)
+            return fail(h, LBM_EINVAL, "unsupported tile shape");
+        CK(h, e);
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
+    if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    const int nb = (int)((h->ncols + 127) / 128);
+    k_obs_columns<<<nb, 128, 0, h->stream>>>(
+        h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
+        h->d_mom[h->cur], h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
+    k_obs_reduce<<<h->count, 256, 0, h->stream>>>(
+        h->d_desc, h->d_col_base, h->d_cols, h->d_wall0, h->d_st, h->steps,
+        (LbmObsDev *)h->d_obs);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->d_obs, h->count * sizeof(lbm_obs),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    int kerr = 0;
+    CK(h, cudaMemcpy(&kerr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kerr) {
+        h->dead = true;
+        return fail(h, LBM_ETIMEOUT, "a bounded wait in the step kernel ran out");
+    }
+    for (int l = 0; l < h->count; ++l)
+        if (out[l].nonfinite)
+            return fail(h, LBM_ENAN, "non-finite density in lattice " + std::to_string(l));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k,
+                                         uint8_t *host, size_t n) {
+    if (!h || !host || k < 0 || k >= h->count) return fail(h, LBM_EINVAL, "bad argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    const LatDesc &d = h->desc[k];
+    if (n != (size_t)d.nx * d.ny) return fail(h, LBM_EINVAL, "size mismatch");
+    std::vector<uint8_t> raw(d.plane);
+    CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, d.plane,
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const MaskBits mb(h->steps);
+    for (int y = 0; y < d.ny; ++y)
+        for (int x = 0; x < d.nx; ++x)
+            host[(size_t)y * d.nx + x] = (raw[(size_t)y * d.pitch + x] & mb.force) ? 1 : 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
+                                     void *host, size_t bytes) {
+    if (!h || !host || k < 0 || k >= h->count) return fail(h, LBM_EINVAL, "bad argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    const LatDesc &d = h->desc[k];
+    const size_t N = (size_t)d.nx * d.ny;
+    size_t need = which == LBM_FIELD_POPS ? NPOP * N * 4
+                : which == LBM_FIELD_DEPOSIT ? N * 8
+                : which == LBM_FIELD_DENSITY ? 3 * N * 4 : 0;
+    if (need == 0) return fail(h, LBM_EINVAL, "unknown field");
+    if (bytes != need) return fail(h, LBM_EINVAL, "size mismatch");
+    dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
+    k_export<<<grid, blk, 0, h->stream>>>(
+        h->d_desc, k, h->d_pop[h->cur], h->d_mom[h->cur], h->d_mask, h->d_m,
+        h->steps, h->half, which == LBM_FIELD_POPS ? h->d_canon : nullptr,
+        which == LBM_FIELD_DENSITY ? h->d_dens : nullptr,
+        which == LBM_FIELD_DEPOSIT ? h->d_dep : nullptr);
+    CK(h, cudaGetLastError());
+    const void *src = which == LBM_FIELD_POPS ? (const void *)h->d_canon
+                    : which == LBM_FIELD_DENSITY ? (const void *)h->d_dens
+                    : (const void *)h->d_dep;
+    CK(h, cudaMemcpyAsync(host, src, need, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+// Folds pending flips of lattice k into its ledger and aligns its mask bits.
+static lbm_status settle(lbm_handle *h, int k) {
+    const LatDesc &d = h->desc[k];
+    dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
+    k_settle<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_pop[h->cur],
+                                         h->d_mom[h->cur], h->d_mask, h->d_m,
+                                         h->d_st, h->steps, h->half);
+    k_mask_agree<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_mask, h->steps);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
+                                     const void *host, size_t bytes) {
+    if (!h || !host || k < 0 || k >= h->count) return fail(h, LBM_EINVAL, "bad argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    const LatDesc &d = h->desc[k];
+    const size_t N = (size_t)d.nx * d.ny;
+    if (which == LBM_FIELD_POPS) {
+        if (bytes != NPOP * N * 4) return fail(h, LBM_EINVAL, "size mismatch");
+        lbm_status s = settle(h, k);
+        if (s != LBM_OK) return s;
+        CK(h, cudaMemcpyAsync(h->d_canon, host, bytes, cudaMemcpyHostToDevice, h->stream));
+        dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
+        const MaskBits mb(h->steps);
+        k_unstream<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_canon, h->d_mask,
+                                               mb.force, h->d_pop[h->cur],
+                                               h->d_mom[h->cur], h->half);
+        CK(h, cudaGetLastError());
+        CK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    if (which == LBM_FIELD_DEPOSIT) {
+        if (bytes != N * 8) return fail(h, LBM_EINVAL, "size mismatch");
+        lbm_status s = settle(h, k);
+        if (s != LBM_OK) return s;
+        std::vector<uint8_t> raw(d.plane);
+        CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, d.plane,
+                              cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        std::vector<double> m(d.plane, 0.0);
+        const double *src = static_cast<const double *>(host);
+        for (int y = 0; y < d.ny; ++y)
+            for (int x = 0; x < d.nx; ++x)
+                if (!(raw[(size_t)y * d.pitch + x] & 7))
+                    m[(size_t)y * d.pitch + x] = src[(size_t)y * d.nx + x];
+        CK(h, cudaMemcpyAsync(h->d_m + d.node_off, m.data(), d.plane * 8,
+                              cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    return fail(h, LBM_EINVAL, "field cannot be set");
+}
+
+// ---- checkpoints -----------------------------------------------------------
+
+static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t count, half;
+    int64_t pop_elems, mom_elems, node_elems, nsec, steps;
+    int32_t cur, pad;
+};
+
+extern "C" lbm_status lbm_save(lbm_handle *h, const char *path) {
+    if (!h || !path) return fail(h, LBM_EINVAL, "NULL argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    CK(h, cudaStreamSynchronize(h->stream));
+    const size_t esz = h->half ? 2 : 4;
+    CkptHeader hd;
+    memcpy(hd.magic, kMagic, 8);
+    hd.count = h->count;
+    hd.half = h->half;
+    hd.pop_elems = h->pop_elems;
+    hd.mom_elems = h->half ? h->mom_elems : 0;
+    hd.node_elems = h->node_elems;
+    hd.nsec = h->nsec;
+    hd.steps = h->steps;
+    hd.cur = 0;
+    hd.pad = 0;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(h, LBM_EIO, std::string("cannot open ") + path);
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && fwrite(h->desc.data(), sizeof(LatDesc), h->count, f) == (size_t)h->count;
+    auto dump = [&](const void *dptr, size_t bytes) {
+        if (!ok) return;
+        std::vector<uint8_t> buf(std::min<size_t>(bytes, (size_t)1 << 28));
+        size_t done = 0;
+        while (ok && done < bytes) {
+            const size_t n = std::min(buf.size(), bytes - done);
+            if (cudaMemcpy(buf.data(), (const uint8_t *)dptr + done, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                ok = false;
+                return;
+            }
+            ok = fwrite(buf.data(), 1, n, f) == n;
+            done += n;
+        }
+    };
+    dump(h->d_pop[h->cur], h->pop_elems * esz);
+    if (h->half) dump(h->d_mom[h->cur], h->mom_elems * 2);
+    dump(h->d_mask, h->node_elems);
+    dump(h->d_m, h->node_elems * 8);
+    dump(h->d_col_fluid, h->nsec * 4);
+    dump(h->d_st, h->count * sizeof(LatState));
+    dump(h->d_step, 8);
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(h, LBM_EIO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
+    if (!h || !path) return fail(h, LBM_EINVAL, "NULL argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    CK(h, cudaStreamSynchronize(h->stream));
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(h, LBM_EIO, std::string("cannot open ") + path);
+    CkptHeader hd;
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, kMagic, 8) == 0;
+    ok = ok && hd.count == h->count && hd.half == (int)h->half &&
+         hd.pop_elems == h->pop_elems && hd.node_elems == h->node_elems &&
+         hd.nsec == h->nsec;
+    std::vector<LatDesc> dsc(h->count);
+    ok = ok && fread(dsc.data(), sizeof(LatDesc), h->count, f) == (size_t)h->count;
+    if (ok) {
+        for (int l = 0; l < h->count; ++l)
+            if (memcmp(&dsc[l], &h->desc[l], sizeof(LatDesc)) != 0) ok = false;
+    }
+    if (!ok) {
+        fclose(f);
+        return fail(h, LBM_EINVAL, "checkpoint does not match this handle");
+    }
+    const size_t esz = h->half ? 2 : 4;
+    auto slurp = [&](void *dptr, size_t bytes) {
+        if (!ok) return;
+        std::vector<uint8_t> buf(std::min<size_t>(bytes, (size_t)1 << 28));
+        size_t done = 0;
+        while (ok && done < bytes) {
+            const size_t n = std::min(buf.size(), bytes - done);
+            ok = fread(buf.data(), 1, n, f) == n;
+            if (ok && cudaMemcpy((uint8_t *)dptr + done, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess)
+                ok = false;
+            done += n;
+        }
+    };
+    h->cur = 0;
+    slurp(h->d_pop[0], h->pop_elems * esz);
+    if (h->half) slurp(h->d_mom[0], h->mom_elems * 2);
+    slurp(h->d_mask, h->node_elems);
+    slurp(h->d_m, h->node_elems * 8);
+    slurp(h->d_col_fluid, h->nsec * 4);
+    slurp(h->d_st, h->count * sizeof(LatState));
+    slurp(h->d_step, 8);
+    fclose(f);
+    if (!ok) return fail(h, LBM_EIO, std::string("read failed: ") + path);
+    h->steps = hd.steps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_fit_reff(const double *t, const double *z,
+                                   int32_t n, double gamma, double mu,
+                                   double length, double cos_theta0,
+                                   double *r_eff) {
+    if (!t || !z || !r_eff || n < 2 || !(gamma > 0) || !(cos_theta0 != 0))
+        return LBM_EINVAL;
+    double st = 0, sz = 0;
+    for (int i = 0; i < n; ++i) { st += t[i]; sz += z[i]; }
+    const double mt = st / n, mz = sz / n;
+    double num = 0, den = 0;
+    for (int i = 0; i < n; ++i) {
+        num += (t[i] - mt) * (z[i] - mz);
+        den += (t[i] - mt) * (t[i] - mt);
+    }
+    if (!(den > 0)) return LBM_EINVAL;
+    const double v = num / den;
+    *r_eff = 3.0 * mu * length * v / (gamma * cos_theta0);
+    return LBM_OK;
+}

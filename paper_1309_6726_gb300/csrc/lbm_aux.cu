@@ -1,0 +1,400 @@
+// lbm_aux.cu -- kernels around the time step: building the stored state
+// from post-streaming fields (initial state, user-set fields, loading),
+// reading it back as post-streaming fields, and the observables of the
+// paper's Sec. III (front, wetted length, radii, Delta e, masses, closure).
+//
+// The step kernel stores the post-collision populations of the last step
+// (pull scheme).  The post-streaming state f(t) the method is stated in is
+// therefore one pull away; "unstream" is its exact inverse:
+//   f*_i(x) = f_i(x + e_i)        if x + e_i is fluid,
+//   f*_i(x) = f_{opp i}(x)        if x + e_i is solid (it bounced back).
+#include "lbm_device.cuh"
+
+namespace lbmk {
+
+__device__ __forceinline__ float load_pop(const void *base, const __half *mom,
+                                          const LatDesc &d, bool half, int q,
+                                          int64_t e) {
+    if (!half) return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
+    const float dv = __half2float(static_cast<const __half *>(base)[d.pop_off + q * d.plane + e]);
+    const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
+    const float rt = __half2float(mom[d.mom_off + comp * d.plane + e]);
+    return comp < 2 ? wq(q - comp * Q) * (rt + dv) : 0.25f * (rt + dv);
+}
+
+// Post-streaming populations of node (x, y) at the current step: 22 values
+// (A, B, solute), pulled from the stored post-collision state with the
+// streaming mask bit.
+__device__ __forceinline__ void pull_node(const void *fin, const __half *mom,
+                                          const uint8_t *mask,
+                                          const LatDesc &d, bool half,
+                                          uint8_t pullbit, int x, int y,
+                                          float out[NPOP]) {
+    const int nx = d.nx, ny = d.ny;
+    const int64_t own = (int64_t)y * d.pitch + x;
+    for (int i = 0; i < Q; ++i) {
+        const int xs = wrap1(x - cx(i), nx), ys = wrap1(y - cy(i), ny);
+        const int64_t src = (int64_t)ys * d.pitch + xs;
+        const bool b = i != 0 && (mask[src] & pullbit);
+        out[i] = load_pop(fin, mom, d, half, b ? opp(i) : i, b ? own : src);
+        out[Q + i] = load_pop(fin, mom, d, half, Q + (b ? opp(i) : i), b ? own : src);
+    }
+    for (int k = 0; k < QS; ++k) {
+        const int xs = wrap1(x - sx(k), nx), ys = wrap1(y - sy(k), ny);
+        const int64_t src = (int64_t)ys * d.pitch + xs;
+        const bool b = mask[src] & pullbit;
+        out[2 * Q + k] = load_pop(fin, mom, d, half, 2 * Q + (b ? sopp(k) : k), b ? own : src);
+    }
+}
+
+// Writes the stored form of node (x, y) from its 22 post-collision values.
+__device__ __forceinline__ void store_node(void *fout, __half *mout,
+                                           const LatDesc &d, bool half,
+                                           int64_t own, const float v[NPOP]) {
+    if (!half) {
+        float *f = static_cast<float *>(fout);
+        for (int q = 0; q < NPOP; ++q) f[d.pop_off + q * d.plane + own] = v[q];
+        return;
+    }
+    __half *f = static_cast<__half *>(fout);
+    for (int comp = 0; comp < 2; ++comp) {
+        float r = 0.f;
+        for (int i = 0; i < Q; ++i) r += v[comp * Q + i];
+        const __half rh = __float2half_rn(r);
+        const float rt = __half2float(rh);
+        mout[d.mom_off + comp * d.plane + own] = rh;
+        for (int i = 0; i < Q; ++i)
+            f[d.pop_off + (comp * Q + i) * d.plane + own] =
+                __float2half_rn(v[comp * Q + i] * (1.0f / wq(i)) - rt);
+    }
+    const float c = v[18] + v[19] + v[20] + v[21];
+    const __half ch = __float2half_rn(c);
+    const float ct = __half2float(ch);
+    mout[d.mom_off + 2 * d.plane + own] = ch;
+    for (int k = 0; k < QS; ++k)
+        f[d.pop_off + (2 * Q + k) * d.plane + own] = __float2half_rn(4.0f * v[18 + k] - ct);
+}
+
+// canonical layout of one lattice: [22][ny][nx] floats, no padding.
+__global__ void k_rest_state(const LatDesc *desc, int l, const float *rho_a,
+                             const float *rho_b, const float *conc,
+                             const uint8_t *solid, float *canon) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const int64_t n = (int64_t)y * d.nx + x;
+    const int64_t P = (int64_t)d.nx * d.ny;
+    const bool fl = solid[n] == 0;
+    const float ra = fl ? rho_a[n] : 0.f, rb = fl ? rho_b[n] : 0.f;
+    const float c = fl ? conc[n] : 0.f;
+    for (int i = 0; i < Q; ++i) {
+        canon[i * P + n] = wq(i) * ra;
+        canon[(Q + i) * P + n] = wq(i) * rb;
+    }
+    for (int k = 0; k < QS; ++k) canon[(2 * Q + k) * P + n] = 0.25f * c;
+}
+
+// Stored state from post-streaming fields (exact inverse of the pull).
+// The mask must hold no pending flip (force bit == streaming bit).
+__global__ void k_unstream(const LatDesc *desc, int l, const float *canon,
+                           const uint8_t *mask_all, uint8_t forcebit,
+                           void *fout, __half *mout, bool half) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const uint8_t *mask = mask_all + d.node_off;
+    const int64_t own = (int64_t)y * d.pitch + x;
+    if (mask[own] & forcebit) return;
+    const int64_t P = (int64_t)d.nx * d.ny;
+    float v[NPOP];
+    for (int i = 0; i < Q; ++i) {
+        const int xd = wrap1(x + cx(i), d.nx), yd = wrap1(y + cy(i), d.ny);
+        const bool b = mask[(int64_t)yd * d.pitch + xd] & forcebit;
+        const int64_t src = b ? (int64_t)y * d.nx + x : (int64_t)yd * d.nx + xd;
+        const int qi = b ? opp(i) : i;
+        v[i] = canon[qi * P + src];
+        v[Q + i] = canon[(Q + qi) * P + src];
+    }
+    for (int k = 0; k < QS; ++k) {
+        const int xd = wrap1(x + sx(k), d.nx), yd = wrap1(y + sy(k), d.ny);
+        const bool b = mask[(int64_t)yd * d.pitch + xd] & forcebit;
+        const int64_t src = b ? (int64_t)y * d.nx + x : (int64_t)yd * d.nx + xd;
+        v[2 * Q + k] = canon[(2 * Q + (b ? sopp(k) : k)) * P + src];
+    }
+    store_node(fout, mout, d, half, own, v);
+}
+
+// Post-streaming fields of lattice l at step t into canon ([22][ny][nx]);
+// dens ([3][ny][nx]: rho_A, rho_B, C) and dep ([ny][nx]) when not NULL.
+// Nodes solid in s_t (including those turned solid last step) read zero.
+__global__ void k_export(const LatDesc *desc, int l, const void *fin,
+                         const __half *min_, const uint8_t *mask_all,
+                         const double *m_all, long long t, bool half,
+                         float *canon, float *dens, double *dep) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const MaskBits mb(t);
+    const uint8_t *mask = mask_all + d.node_off;
+    const int64_t own = (int64_t)y * d.pitch + x;
+    const int64_t n = (int64_t)y * d.nx + x;
+    const int64_t P = (int64_t)d.nx * d.ny;
+    const bool solid = mask[own] & mb.force;
+    float v[NPOP];
+    if (solid) {
+        for (int q = 0; q < NPOP; ++q) v[q] = 0.f;
+    } else {
+        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+    }
+    if (canon)
+        for (int q = 0; q < NPOP; ++q) canon[q * P + n] = v[q];
+    if (dens) {
+        float ra = 0.f, rb = 0.f;
+        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+        dens[n] = ra;
+        dens[P + n] = rb;
+        dens[2 * P + n] = v[18] + v[19] + v[20] + v[21];
+    }
+    if (dep) dep[n] = solid ? 0.0 : m_all[d.node_off + own];
+}
+
+// Folds nodes turned solid in the last step into the ledger now and makes
+// the three mask bits agree (used before replacing fields, so that the
+// stored state has no pending flip).
+__global__ void k_settle(const LatDesc *desc, int l, const void *fin,
+                         const __half *min_, uint8_t *mask_all, double *m_all,
+                         LatState *st, long long t, bool half) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const MaskBits mb(t);
+    uint8_t *mask = mask_all + d.node_off;
+    const int64_t own = (int64_t)y * d.pitch + x;
+    const uint8_t s = mask[own];
+    if ((s & mb.force) && !(s & mb.pull)) {
+        float v[NPOP];
+        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        double ra = 0, rb = 0;
+        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+        const double c = (double)v[18] + v[19] + v[20] + v[21];
+        double *mp = m_all + d.node_off + own;
+        atomicAdd(&st[l].ledger[0], ra);
+        atomicAdd(&st[l].ledger[1], rb);
+        atomicAdd(&st[l].ledger[2], c);
+        atomicAdd(&st[l].ledger[3], *mp);
+        *mp = 0.0;
+    }
+}
+
+__global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
+                             long long t) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const MaskBits mb(t);
+    uint8_t *mask = mask_all + d.node_off;
+    const int64_t own = (int64_t)y * d.pitch + x;
+    mask[own] = (mask[own] & mb.force) ? 7 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Observables.  Pass 1: one thread per column of every lattice (columns of
+// all lattices are numbered consecutively through col_base) walks the
+// column and writes a ColObs.  Pass 2: one block per lattice reduces them.
+// ---------------------------------------------------------------------------
+
+__global__ void k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
+                              const int64_t *col_base, int ncols_total,
+                              const void *fin, const __half *min_,
+                              const uint8_t *mask_all, const double *m_all,
+                              long long t, bool half, ColObs *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols_total) return;
+    const int l = col_lat[c];
+    const LatDesc d = desc[l];
+    const int x = (int)(c - col_base[l]);
+    const MaskBits mb(t);
+    const uint8_t *mask = mask_all + d.node_off;
+    const int ny = d.ny;
+    const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
+    ColObs o = {};
+    int lo = -1;
+    bool below = true;
+    int b = 0, tt = 0;
+    float v[NPOP];
+    for (int y = 0; y < ny; ++y) {
+        const int64_t own = (int64_t)y * d.pitch + x;
+        const uint8_t s = mask[own];
+        const bool solid = s & mb.force;
+        if (solid) {
+            if (below) ++b;
+            ++tt;
+            if (!(s & mb.pull)) {  // turned solid at the end of the last step
+                pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+                double ra = 0, rb = 0;
+                for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+                o.pend_a += ra;
+                o.pend_b += rb;
+                o.pend_c += (double)v[18] + v[19] + v[20] + v[21];
+                o.pend_m += m_all[d.node_off + own];
+            }
+            continue;
+        }
+        below = false;
+        tt = 0;
+        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        float ra = 0.f, rb = 0.f;
+        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+        const float cc = v[18] + v[19] + v[20] + v[21];
+        if (!(ra + rb < 3.0e38f)) o.nonfinite = 1;
+        o.mass_a += ra;
+        o.mass_b += rb;
+        o.mass_c += cc;
+        o.mass_m += m_all[d.node_off + own];
+        o.h += 1;
+        if (lo < 0) { lo = y; o.wet_lo = ra > rb; }
+        o.wet_hi = ra > rb;
+        if (y == yc0) { o.phi0 = ra - rb; o.fl0 = 1; }
+        if (y == yc1) { o.phi1 = ra - rb; o.fl1 = 1; }
+    }
+    o.b = b;
+    o.t = tt;
+    if (o.h == 0) { o.b = ny; o.t = ny; o.wet_lo = o.wet_hi = 0; }
+    out[c] = o;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] += sh[tid + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+struct LbmObsDev {  // mirrors lbm_obs of the public header
+    long long step;
+    double front, wetted_lower, wetted_upper, r_min, r_h, r_ave, delta_e;
+    double precip_mass, mass_a, mass_b, mass_c;
+    double ledger_a, ledger_b, ledger_c, ledger_m;
+    int closed, nonfinite;
+    long long closure_step;
+};
+
+// blockDim.x must be 256.
+__global__ void k_obs_reduce(const LatDesc *desc, const int64_t *col_base,
+                             const ColObs *cols, const int16_t *wall0,
+                             const LatState *st, long long t,
+                             LbmObsDev *out) {
+    __shared__ double sh[256];
+    __shared__ int s_first[2];
+    __shared__ int s_min_h;
+    const int l = blockIdx.x;
+    const LatDesc d = desc[l];
+    const ColObs *c = cols + col_base[l];
+    const int tid = threadIdx.x;
+    const int nx = d.nx, ny = d.ny;
+    const int x0 = d.cap_x0, x1 = d.cap_x1, ncap = x1 - x0;
+    const int16_t *w0 = wall0 + 2 * d.col_off;  // (b0, t0) per section column
+    if (tid == 0) { s_first[0] = s_first[1] = 0x7fffffff; s_min_h = 0x7fffffff; }
+    __syncthreads();
+    double ma = 0, mb = 0, mc = 0, mm = 0, pa = 0, pb = 0, pc = 0, pm = 0;
+    int nonfin = 0;
+    for (int x = tid; x < nx; x += blockDim.x) {
+        const ColObs &o = c[x];
+        ma += o.mass_a; mb += o.mass_b; mc += o.mass_c; mm += o.mass_m;
+        pa += o.pend_a; pb += o.pend_b; pc += o.pend_c; pm += o.pend_m;
+        nonfin |= o.nonfinite;
+        // front: first x >= x0 - 1 (<= nx - 2) with a + to - crossing
+        if (x >= max(x0 - 1, 0) && x <= nx - 2) {
+            const ColObs &o1 = c[x + 1];
+            if (o.fl0 && o1.fl0 && o.phi0 > 0.f && o1.phi0 <= 0.f) atomicMin(&s_first[0], x);
+            if (o.fl1 && o1.fl1 && o.phi1 > 0.f && o1.phi1 <= 0.f) atomicMin(&s_first[1], x);
+        }
+    }
+    double area = 0, perim = 0, hsum = 0, de = 0, wl = 0, wu = 0;
+    int closed = 0;
+    const double yc = (ny - 1) / 2.0;
+    for (int k = tid; k < ncap; k += blockDim.x) {
+        const ColObs &o = c[x0 + k];
+        const int b0 = w0[2 * k], t0 = w0[2 * k + 1];
+        atomicMin(&s_min_h, o.h);
+        hsum += o.h;
+        double g;
+        if (o.h == 0) {
+            closed = 1;
+            g = (ny - b0 - t0) / 2.0;
+        } else {
+            g = (double)max(o.b - b0, o.t - t0);
+            wl += o.wet_lo;
+            wu += o.wet_hi;
+        }
+        de = fmax(de, g);
+        area += fmax(0.0, yc - (o.b - 0.5));
+        perim += 1.0;
+        if (k + 1 < ncap) perim += fabs((double)(c[x0 + k + 1].b - o.b));
+    }
+    ma = block_sum(ma, sh); mb = block_sum(mb, sh); mc = block_sum(mc, sh);
+    mm = block_sum(mm, sh); pa = block_sum(pa, sh); pb = block_sum(pb, sh);
+    pc = block_sum(pc, sh); pm = block_sum(pm, sh);
+    area = block_sum(area, sh); perim = block_sum(perim, sh);
+    hsum = block_sum(hsum, sh); wl = block_sum(wl, sh); wu = block_sum(wu, sh);
+    // max of de, or of flags, by negated / summed reductions
+    sh[tid] = de;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] = fmax(sh[tid], sh[tid + s]);
+        __syncthreads();
+    }
+    de = sh[0];
+    __syncthreads();
+    const double nclosed = block_sum((double)closed, sh);
+    const double nnonfin = block_sum((double)nonfin, sh);
+    if (tid == 0) {
+        LbmObsDev r;
+        r.step = t;
+        double z[2];
+        const int rows[2] = {(ny - 1) / 2, ny / 2};
+        for (int k = 0; k < 2; ++k) {
+            const int xf = s_first[k];
+            if (xf == 0x7fffffff) {
+                z[k] = nan("");
+            } else {
+                const float p0 = rows[k] == rows[0] ? c[xf].phi0 : c[xf].phi1;
+                const float p1 = rows[k] == rows[0] ? c[xf + 1].phi0 : c[xf + 1].phi1;
+                z[k] = xf + (double)p0 / ((double)p0 - (double)p1) - (x0 - 0.5);
+            }
+        }
+        r.front = rows[0] == rows[1] ? z[0] : 0.5 * (z[0] + z[1]);
+        r.wetted_lower = wl;
+        r.wetted_upper = wu;
+        r.r_min = ncap > 0 ? s_min_h / 2.0 : 0.0;
+        r.r_ave = ncap > 0 ? hsum / ncap / 2.0 : 0.0;
+        r.r_h = perim > 0 ? area / perim : 0.0;
+        r.delta_e = de;
+        const LatState s = st[l];
+        r.ledger_a = s.ledger[0] + pa;
+        r.ledger_b = s.ledger[1] + pb;
+        r.ledger_c = s.ledger[2] + pc;
+        r.ledger_m = s.ledger[3] + pm;
+        r.precip_mass = mm + r.ledger_m;
+        r.mass_a = ma;
+        r.mass_b = mb;
+        r.mass_c = mc;
+        r.closed = nclosed > 0;
+        r.nonfinite = (nnonfin > 0) || s.nonfinite;
+        r.closure_step = s.closure == ~0ull ? -1 : (long long)s.closure;
+        out[l] = r;
+    }
+}
+
+}  // namespace lbmk

@@ -1,0 +1,126 @@
+// lbm_device.cuh -- device-side layout and lattice constants of the
+// reactive two-component lattice Boltzmann library (sm_103a).
+//
+// Layout in HBM (one handle, `count` lattices packed back to back):
+//   populations: two ping-pong buffers; in each, lattice l owns 22
+//     consecutive planes of ny*pitch elements (A: 9, B: 9, solute: 4),
+//     rows padded to `pitch` (a multiple of 32 elements, so every row
+//     starts on a 128-byte boundary in FP32 storage);
+//   FP16 storage adds 3 moment planes per lattice and buffer (rho_A,
+//     rho_B, C rounded to FP16) that the deviations are taken from;
+//   mask: one byte per node, read and written in place (see MaskBits);
+//   deposit: one double per node;
+//   per section column: fluid-node counter (closure), initial wall
+//     thickness below and above (observables);
+//   per lattice: ledgers, closure step, non-finite flag.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace lbmk {
+
+constexpr int Q = 9;      // D2Q9 per fluid component
+constexpr int QS = 4;     // D2Q4 solute
+constexpr int NPOP = 22;  // 9 + 9 + 4 planes per lattice
+constexpr int NMOM = 3;   // FP16 storage: rho_A, rho_B, C planes
+
+// D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+__host__ __device__ __forceinline__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+__host__ __device__ __forceinline__ constexpr float wq(int i) {
+    return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// D2Q4 order (1,0) (0,1) (-1,0) (0,-1).
+__host__ __device__ __forceinline__ constexpr int sx(int k) {
+    return k == 0 ? 1 : (k == 2 ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int sy(int k) {
+    return k == 1 ? 1 : (k == 3 ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int sopp(int k) { return (k + 2) & 3; }
+
+// The mask byte keeps the solid set of three consecutive steps in three
+// rotating bits.  Before the kernel of step t (t steps completed) runs, bit
+// t%3 holds s_t (the solid set the forces, adhesion and reaction of step t
+// see) and bit (t+2)%3 holds s_{t-1} (the set the streaming that ends step
+// t-1 used, which the pull of step t replays).  Step t writes s_{t+1} into
+// bit (t+1)%3, which held s_{t-2}: no reader of step t looks at that bit,
+// so the in-place update is race free, and since solid only grows a node's
+// byte changes on at most three steps after it is flagged.
+struct MaskBits {
+    uint8_t force, pull, next;
+    __host__ __device__ explicit MaskBits(int64_t t) {
+        int p = (int)(t % 3);
+        force = (uint8_t)(1u << p);
+        pull = (uint8_t)(1u << ((p + 2) % 3));
+        next = (uint8_t)(1u << ((p + 1) % 3));
+    }
+};
+
+// One lattice of the batch.
+struct LatDesc {
+    int32_t nx, ny, pitch, tiles_x;
+    int32_t tile_base, cap_x0, cap_x1, inlet;
+    int64_t node_off;   // first node of this lattice in mask / deposit
+    int64_t pop_off;    // first element of plane 0 in a population buffer
+    int64_t mom_off;    // first element of moment plane 0 (FP16 storage)
+    int64_t plane;      // ny * pitch
+    int64_t col_off;    // first section column in per-column arrays
+    float tau_a, tau_b, inv_tau_a, inv_tau_b, inv_tau_d;
+    float g_coh, g_ads, k_r, c_in, body_x;
+    double m_th;
+};
+
+struct LatState {
+    double ledger[4];               // A, B, solute, deposit moved by growth
+    unsigned long long closure;     // first closure step count, ~0 if none
+    int32_t nonfinite;
+    int32_t pad;
+};
+
+// Per-column partial results of the observables pass.
+struct ColObs {
+    double mass_a, mass_b, mass_c, mass_m;     // fluid content (s_t)
+    double pend_a, pend_b, pend_c, pend_m;     // nodes turned solid last step
+    float phi0, phi1;                           // rho_A - rho_B, centerline
+    int32_t h, b, t;                            // aperture, wall thickness
+    int32_t wet_lo, wet_hi;                     // A majority at wall nodes
+    int32_t fl0, fl1;                           // centerline rows fluid
+    int32_t nonfinite;
+};
+
+struct StepArgs {
+    const LatDesc *desc;
+    const int32_t *tile_lat;
+    const void *fin;        // post-collision populations of the last step
+    void *fout;             // post-collision populations of this step
+    const __half *min_;     // FP16 storage: moment planes of fin
+    __half *mout;           // FP16 storage: moment planes of fout
+    uint8_t *mask;
+    double *m;
+    int32_t *col_fluid;
+    LatState *st;
+    int64_t *step;          // completed steps (read at start, bumped at end)
+    unsigned int *done;     // blocks finished in this launch
+};
+
+// Periodic index for any offset (lattices smaller than a tile included).
+__device__ __forceinline__ int wrapg(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+// Periodic index for a neighbour offset of at most one.
+__device__ __forceinline__ int wrap1(int a, int n) {
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+}  // namespace lbmk

@@ -1,0 +1,233 @@
+// lbm_step.cu -- the fused reactive lattice Boltzmann time step (sm_103a).
+//
+// One launch advances every lattice of a handle by one step.  A block owns
+// a TX x TY tile of one lattice and does, per node, the whole step of the
+// paper's Sec. II model in one pass over HBM:
+//   1. pull-streaming with half-way bounce-back of the 9 + 9 populations
+//      (each read once), giving the post-streaming state of this step;
+//   2. densities of the tile plus a one-node ring (the ring's pulls are
+//      L2 hits: neighbouring tiles read the same lines), kept in shared
+//      memory for the cohesion stencil;
+//   3. Martys-Chen cohesion and adhesion forces, Shan-Chen velocity shift,
+//      BGK collision of both components;
+//   4. pull of the D2Q4 solute, its BGK collision with the barycentric
+//      velocity (inlet column imposed), first-order surface reaction;
+//   5. FP64 deposit update and threshold test; a node that reaches it is
+//      flagged in the mask (turns solid for the next step's forces, keeps
+//      the streaming of this step -- see MaskBits);
+//   6. a node flagged in the previous step hands its post-streaming fluid,
+//      solute and deposit to the lattice ledger instead of colliding.
+// The solid mask and the deposit are read only as a byte per node and a
+// double per reacting node; populations of solid nodes are never touched.
+//
+// Floating point: FP32 arithmetic in the order of the collision formulas;
+// the deposit and its threshold test are FP64.  Populations are stored as
+// FP32 (Store32) or as FP16 deviations (Store16, see below).
+#include "lbm_node.cuh"
+
+namespace lbmk {
+
+template <int TX, int TY>
+struct Tile {
+    static constexpr int NT = TX * TY;
+    static constexpr int HX = TX + 4, HY = TY + 4;  // mask halo, radius 2
+    static constexpr int RX = TX + 2, RY = TY + 2;  // density frame, radius 1
+    static constexpr int NRING = 2 * RX + 2 * TY;
+};
+
+// Bounce-back bits of the 9 pulls of the node at mask-halo slot (hy, hx):
+// bit i set when the source x - e_i was solid for the streaming.
+template <int HX>
+__device__ __forceinline__ unsigned pull_bits(const uint8_t (*sm)[HX], int hy,
+                                              int hx, uint8_t pullbit) {
+    unsigned bb = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (sm[hy - cy(i)][hx - cx(i)] & pullbit) bb |= 1u << i;
+    return bb;
+}
+
+// Pulls the 9 populations of component `comp` into node (gx, gy).
+template <class S>
+__device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
+                                      const __half *__restrict__ mom,
+                                      const LatDesc &d, int comp, int gx,
+                                      int gxm, int gxp, int gy, int gym,
+                                      int gyp, unsigned bb, float f[Q]) {
+    const int64_t own = (int64_t)gy * d.pitch + gx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sxx = cx(i) > 0 ? gxm : (cx(i) < 0 ? gxp : gx);
+        const int syy = cy(i) > 0 ? gym : (cy(i) < 0 ? gyp : gy);
+        const bool b = (bb >> i) & 1u;
+        const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
+        const int q = comp * Q + (b ? opp(i) : i);
+        if constexpr (!S::kHalf) {
+            f[i] = __ldg(fin + d.pop_off + q * d.plane + src);
+        } else {
+            const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
+            const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
+            f[i] = wq(i) * (rt + dv);
+        }
+    }
+}
+
+// Pulls the 4 solute populations into node (gx, gy); bounce-back where the
+// D2Q4 source was solid.
+template <class S>
+__device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
+                                      const __half *__restrict__ mom,
+                                      const LatDesc &d, int gx, int gxm,
+                                      int gxp, int gy, int gym, int gyp,
+                                      unsigned bb4, float g[QS]) {
+    const int64_t own = (int64_t)gy * d.pitch + gx;
+#pragma unroll
+    for (int k = 0; k < QS; ++k) {
+        const int sxx = sx(k) > 0 ? gxm : (sx(k) < 0 ? gxp : gx);
+        const int syy = sy(k) > 0 ? gym : (sy(k) < 0 ? gyp : gy);
+        const bool b = (bb4 >> k) & 1u;
+        const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
+        const int q = 2 * Q + (b ? sopp(k) : k);
+        if constexpr (!S::kHalf) {
+            g[k] = __ldg(fin + d.pop_off + q * d.plane + src);
+        } else {
+            const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
+            const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
+            g[k] = 0.25f * (ct + dv);
+        }
+    }
+}
+
+template <class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    k_step(StepArgs a) {
+    using TL = Tile<TX, TY>;
+    using T = typename S::T;
+    __shared__ uint8_t smask[TL::HY][TL::HX];
+    __shared__ float srho[2][TL::RY][TL::RX];
+    __shared__ long long s_t;
+
+    const int tid = threadIdx.x;
+    const int l = a.tile_lat[blockIdx.x];
+    const LatDesc d = a.desc[l];
+    const T *__restrict__ fin = static_cast<const T *>(a.fin);
+    const int nx = d.nx, ny = d.ny;
+    const int local = blockIdx.x - d.tile_base;
+    const int tx0 = (local % d.tiles_x) * TX;
+    const int ty0 = (local / d.tiles_x) * TY;
+    uint8_t *__restrict__ mask = a.mask + d.node_off;
+
+    if (tid == 0) s_t = *(volatile long long *)a.step;
+    for (int k = tid; k < TL::HY * TL::HX; k += TL::NT) {
+        const int hy = k / TL::HX, hx = k - hy * TL::HX;
+        const int gy = wrapg(ty0 - 2 + hy, ny), gx = wrapg(tx0 - 2 + hx, nx);
+        smask[hy][hx] = mask[(int64_t)gy * d.pitch + gx];
+    }
+    __syncthreads();
+    const long long t = s_t;
+    const MaskBits mb(t);
+
+    // --- own node: pull and density --------------------------------------
+    const int lx = tid % TX, ly = tid / TX;
+    const int x = tx0 + lx, y = ty0 + ly;
+    const bool active = (x < nx) && (y < ny);
+    const int gx = wrapg(x, nx), gy = wrapg(y, ny);
+    const int gxm = wrap1(gx - 1, nx), gxp = wrap1(gx + 1, nx);
+    const int gym = wrap1(gy - 1, ny), gyp = wrap1(gy + 1, ny);
+    const uint8_t s_own = smask[ly + 2][lx + 2];
+    const bool own_pull_fluid = !(s_own & mb.pull);
+    float fA[Q], fB[Q];
+    {
+        float ra = 0.f, rb = 0.f;
+        if (own_pull_fluid) {
+            const unsigned bb = pull_bits<TL::HX>(smask, ly + 2, lx + 2, mb.pull);
+            pull9<S>(fin, a.min_, d, 0, gx, gxm, gxp, gy, gym, gyp, bb, fA);
+            pull9<S>(fin, a.min_, d, 1, gx, gxm, gxp, gy, gym, gyp, bb, fB);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+        }
+        const bool force_solid = s_own & mb.force;
+        srho[0][ly + 1][lx + 1] = force_solid ? 0.f : ra;
+        srho[1][ly + 1][lx + 1] = force_solid ? 0.f : rb;
+    }
+    // --- ring of the density frame ----------------------------------------
+    for (int r = tid; r < TL::NRING; r += TL::NT) {
+        int ry, rx;
+        if (r < TL::RX) { ry = 0; rx = r; }
+        else if (r < 2 * TL::RX) { ry = TL::RY - 1; rx = r - TL::RX; }
+        else if (r < 2 * TL::RX + TY) { ry = 1 + r - 2 * TL::RX; rx = 0; }
+        else { ry = 1 + r - 2 * TL::RX - TY; rx = TL::RX - 1; }
+        const uint8_t s = smask[ry + 1][rx + 1];
+        float ra = 0.f, rb = 0.f;
+        if (!(s & mb.force)) {
+            const int X = wrapg(tx0 - 1 + rx, nx), Y = wrapg(ty0 - 1 + ry, ny);
+            const int Xm = wrap1(X - 1, nx), Xp = wrap1(X + 1, nx);
+            const int Ym = wrap1(Y - 1, ny), Yp = wrap1(Y + 1, ny);
+            const unsigned bb = pull_bits<TL::HX>(smask, ry + 1, rx + 1, mb.pull);
+            float f[Q];
+            pull9<S>(fin, a.min_, d, 0, X, Xm, Xp, Y, Ym, Yp, bb, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ra += f[i];
+            pull9<S>(fin, a.min_, d, 1, X, Xm, Xp, Y, Ym, Yp, bb, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rb += f[i];
+        }
+        srho[0][ry][rx] = ra;
+        srho[1][ry][rx] = rb;
+    }
+    __syncthreads();
+
+    if (active) {
+        const int64_t own = (int64_t)gy * d.pitch + gx;
+        const int hy = ly + 2, hx = lx + 2;
+        unsigned bb4 = 0;
+#pragma unroll
+        for (int k = 0; k < QS; ++k)
+            if (smask[hy - sy(k)][hx - sx(k)] & mb.pull) bb4 |= 1u << k;
+        if (s_own & mb.force) {
+            const uint8_t nb = s_own | mb.next;
+            if (own_pull_fluid) {
+                float g[QS];
+                pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
+                retire_node(a, d, l, own, fA, fB, g);
+            }
+            if (nb != s_own) mask[own] = nb;
+        } else {
+            float g[QS];
+            pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
+            const bool flagged = fluid_update<S>(
+                a, d, l, t, gx, own, fA, fB, g,
+                [&](int c, int i) { return srho[c][ly + 1 + cy(i)][lx + 1 + cx(i)]; },
+                [&](int i) { return (smask[hy + cy(i)][hx + cx(i)] & mb.force) != 0; },
+                [&](int k) { return (smask[hy + sy(k)][hx + sx(k)] & mb.force) != 0; });
+            if (flagged) mask[own] = s_own | mb.next;
+        }
+    }
+    finish_launch(a, t);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+template <int TX, int TY>
+static cudaError_t launch_tile(const StepArgs &a, int ntiles, bool half,
+                               cudaStream_t s) {
+    if (half)
+        k_step<Store16, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+    else
+        k_step<Store32, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
+                               int ty, bool half, cudaStream_t s) {
+    if (tx == 32 && ty == 8) return launch_tile<32, 8>(a, ntiles, half, s);
+    if (tx == 32 && ty == 4) return launch_tile<32, 4>(a, ntiles, half, s);
+    if (tx == 32 && ty == 16) return launch_tile<32, 16>(a, ntiles, half, s);
+    if (tx == 64 && ty == 4) return launch_tile<64, 4>(a, ntiles, half, s);
+    if (tx == 64 && ty == 8) return launch_tile<64, 8>(a, ntiles, half, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbmk

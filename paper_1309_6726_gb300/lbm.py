@@ -1,0 +1,268 @@
+"""Python binding of the CUDA library (``liblbm.so``, C ABI in
+``include/lbm.h``).  Argument marshalling only: every step of the method
+runs in the library's kernels.  There is no fallback: if the library or a
+CUDA device is missing, constructing a :class:`Solver` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENAN, LBM_EIO = \
+    range(7)
+LBM_FP32, LBM_FP16 = 0, 1
+FIELD_POPS, FIELD_DEPOSIT, FIELD_DENSITY = 0, 1, 2
+NPOP = 22
+
+#: exported symbols (every entry point the header declares)
+SYMBOLS = ("lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_step",
+           "lbm_step_count", "lbm_count", "lbm_observables",
+           "lbm_get_solid_mask", "lbm_get_fields", "lbm_set_fields",
+           "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
+           "lbm_fit_reff")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("lbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
+                ("solid", C.POINTER(C.c_uint8)),
+                ("rho_a", C.POINTER(C.c_float)),
+                ("rho_b", C.POINTER(C.c_float)),
+                ("conc", C.POINTER(C.c_float)),
+                ("cap_x0", C.c_int32), ("cap_x1", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("tau_a", C.c_double), ("tau_b", C.c_double),
+                ("tau_d", C.c_double), ("g_coh", C.c_double),
+                ("g_ads", C.c_double), ("k_r", C.c_double),
+                ("m_threshold", C.c_double), ("c_in", C.c_double),
+                ("body_force_x", C.c_double), ("inlet", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("front", C.c_double),
+                ("wetted_lower", C.c_double), ("wetted_upper", C.c_double),
+                ("r_min", C.c_double), ("r_h", C.c_double),
+                ("r_ave", C.c_double), ("delta_e", C.c_double),
+                ("precip_mass", C.c_double), ("mass_a", C.c_double),
+                ("mass_b", C.c_double), ("mass_c", C.c_double),
+                ("ledger_a", C.c_double), ("ledger_b", C.c_double),
+                ("ledger_c", C.c_double), ("ledger_m", C.c_double),
+                ("closed", C.c_int32), ("nonfinite", C.c_int32),
+                ("closure_step", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "liblbm.so not built (run __graft_entry__.build()): %s" % path)
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.lbm_create.argtypes = [C.POINTER(Geometry), C.POINTER(Params),
+                               C.POINTER(vp)]
+    lib.lbm_create_batch.argtypes = [C.POINTER(Geometry), C.POINTER(Params),
+                                     C.c_int32, C.POINTER(vp)]
+    lib.lbm_set_stream.argtypes = [vp, vp]
+    lib.lbm_step.argtypes = [vp, C.c_int64]
+    lib.lbm_step_count.argtypes = [vp]
+    lib.lbm_step_count.restype = C.c_int64
+    lib.lbm_count.argtypes = [vp]
+    lib.lbm_count.restype = C.c_int32
+    lib.lbm_observables.argtypes = [vp, C.POINTER(Obs)]
+    lib.lbm_get_solid_mask.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint8),
+                                       C.c_size_t]
+    lib.lbm_get_fields.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
+    lib.lbm_set_fields.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
+    lib.lbm_save.argtypes = [vp, C.c_char_p]
+    lib.lbm_load.argtypes = [vp, C.c_char_p]
+    lib.lbm_destroy.argtypes = [vp]
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.argtypes = [vp]
+    lib.lbm_last_error.restype = C.c_char_p
+    dp = C.POINTER(C.c_double)
+    lib.lbm_fit_reff.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, dp]
+    _lib = lib
+    return lib
+
+
+def _params(p, precision: int) -> Params:
+    g = p if isinstance(p, dict) else p.as_dict()
+    return Params(g["tau_a"], g["tau_b"], g["tau_d"], g["g_coh"], g["g_ads"],
+                  g["k_r"], g["m_threshold"], g["c_in"], g["body_force_x"],
+                  int(g["inlet"]), int(precision))
+
+
+class Solver:
+    """A batch of lattices on the GPU (one lattice is a batch of one).
+
+    ``geoms`` are :class:`paper_1309_6726_gb300.inputs.Geometry` objects (or
+    anything with ``solid``, ``rho_a``, ``rho_b``, ``conc``, ``cap_x0``,
+    ``cap_x1``) and ``params`` matching :class:`inputs.ModelParams` (or
+    dicts).  ``precision`` is ``"fp32"`` or ``"fp16"``.
+    """
+
+    def __init__(self, geoms, params, precision: str = "fp32"):
+        if not isinstance(geoms, (list, tuple)):
+            geoms, params = [geoms], [params]
+        if len(geoms) != len(params) or not geoms:
+            raise ValueError("need as many params as geometries (>= 1)")
+        self._lib = load_library()
+        prec = {"fp32": LBM_FP32, "fp16": LBM_FP16}[precision]
+        self.precision = precision
+        self._keep = []
+        G = (Geometry * len(geoms))()
+        P = (Params * len(geoms))()
+        self.shapes = []
+        for k, (g, p) in enumerate(zip(geoms, params)):
+            solid = np.ascontiguousarray(g.solid, dtype=np.uint8)
+            ny, nx = solid.shape
+            ra = np.ascontiguousarray(g.rho_a, dtype=np.float32)
+            rb = np.ascontiguousarray(g.rho_b, dtype=np.float32)
+            cc = np.ascontiguousarray(g.conc, dtype=np.float32)
+            self._keep += [solid, ra, rb, cc]
+            G[k] = Geometry(nx, ny, solid.ctypes.data_as(C.POINTER(C.c_uint8)),
+                            ra.ctypes.data_as(C.POINTER(C.c_float)),
+                            rb.ctypes.data_as(C.POINTER(C.c_float)),
+                            cc.ctypes.data_as(C.POINTER(C.c_float)),
+                            int(g.cap_x0), int(g.cap_x1))
+            P[k] = _params(p, prec)
+            self.shapes.append((ny, nx))
+        h = C.c_void_p()
+        st = self._lib.lbm_create_batch(G, P, len(geoms), C.byref(h))
+        self._keep = []
+        if st != LBM_OK:
+            raise LbmError(st, self._lib.lbm_last_error(None).decode())
+        self._h = h
+        self.count = len(geoms)
+
+    # -- life cycle ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != LBM_OK:
+            raise LbmError(st, self._lib.lbm_last_error(self._h).decode())
+
+    # -- stepping ------------------------------------------------------------
+    def set_stream(self, stream) -> None:
+        """Binds a CUDA stream (an int handle, e.g. a torch stream's
+        ``cuda_stream``) or None for the solver's own.  The legacy default
+        stream (handle 0) cannot be bound: it would mean the solver's own."""
+        if stream == 0:
+            raise ValueError("bind a created stream, not the legacy default "
+                             "stream (0)")
+        self._check(self._lib.lbm_set_stream(self._h, stream))
+
+    def step(self, n: int = 1) -> None:
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    @property
+    def step_count(self) -> int:
+        return int(self._lib.lbm_step_count(self._h))
+
+    # -- outputs -------------------------------------------------------------
+    def observables(self, allow_nan: bool = False) -> list[dict]:
+        out = (Obs * self.count)()
+        st = self._lib.lbm_observables(self._h, out)
+        if st == LBM_ENAN and allow_nan:
+            return [o.as_dict() for o in out]
+        self._check(st)
+        return [o.as_dict() for o in out]
+
+    def solid_mask(self, k: int = 0) -> np.ndarray:
+        ny, nx = self.shapes[k]
+        out = np.zeros((ny, nx), np.uint8)
+        self._check(self._lib.lbm_get_solid_mask(
+            self._h, k, out.ctypes.data_as(C.POINTER(C.c_uint8)), out.size))
+        return out
+
+    def populations(self, k: int = 0) -> np.ndarray:
+        """Post-streaming populations (22, ny, nx): A 0-8, B 9-17, solute
+        18-21."""
+        ny, nx = self.shapes[k]
+        out = np.zeros((NPOP, ny, nx), np.float32)
+        self._check(self._lib.lbm_get_fields(self._h, k, FIELD_POPS,
+                                             out.ctypes.data, out.nbytes))
+        return out
+
+    def densities(self, k: int = 0) -> np.ndarray:
+        """(3, ny, nx): rho_A, rho_B, C of the post-streaming state."""
+        ny, nx = self.shapes[k]
+        out = np.zeros((3, ny, nx), np.float32)
+        self._check(self._lib.lbm_get_fields(self._h, k, FIELD_DENSITY,
+                                             out.ctypes.data, out.nbytes))
+        return out
+
+    def deposit(self, k: int = 0) -> np.ndarray:
+        ny, nx = self.shapes[k]
+        out = np.zeros((ny, nx), np.float64)
+        self._check(self._lib.lbm_get_fields(self._h, k, FIELD_DEPOSIT,
+                                             out.ctypes.data, out.nbytes))
+        return out
+
+    def set_populations(self, f, k: int = 0) -> None:
+        a = np.ascontiguousarray(f, dtype=np.float32)
+        ny, nx = self.shapes[k]
+        assert a.size == NPOP * ny * nx
+        self._check(self._lib.lbm_set_fields(self._h, k, FIELD_POPS,
+                                             a.ctypes.data, a.nbytes))
+
+    def set_deposit(self, m, k: int = 0) -> None:
+        a = np.ascontiguousarray(m, dtype=np.float64)
+        self._check(self._lib.lbm_set_fields(self._h, k, FIELD_DEPOSIT,
+                                             a.ctypes.data, a.nbytes))
+
+    def save(self, path: str) -> None:
+        self._check(self._lib.lbm_save(self._h, path.encode()))
+
+    def load(self, path: str) -> None:
+        self._check(self._lib.lbm_load(self._h, path.encode()))
+
+
+def fit_reff(t, z, gamma: float, mu: float, length: float,
+             cos_theta0: float) -> float:
+    """Effective radius from a front history (``lbm_fit_reff``)."""
+    lib = load_library()
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    out = C.c_double()
+    dp = C.POINTER(C.c_double)
+    st = lib.lbm_fit_reff(t.ctypes.data_as(dp), z.ctypes.data_as(dp), len(t),
+                          gamma, mu, length, cos_theta0, C.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_fit_reff: bad arguments")
+    return out.value

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances.  The kernels compute in FP32 and store FP32 (or FP16
+deviations); the oracle computes in FP64.  A population's error is stated
+relative to its lattice weight times a reference density of 1 (the
+majority phase).  FP32: 1e-5 for short runs (a few hundred steps); for the
+2000-step small capillary 1e-4, twice what the oracle's own formulas give
+when evaluated in FP32 (test_fp32_bound.py: the moving meniscus integrates
+FP32 rounding, about 3e-8 per step).  FP16 storage: a measured bound,
+stated with its test.  Integer and index results -- the solid mask, the
+step a node turns solid, the pore-closure step -- must match exactly; the
+front position within 0.5 lattice units.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import analysis as A
+from paper_1309_6726_gb300 import inputs as I
+from paper_1309_6726_gb300 import lbm
+from tests.gpu_helpers import (elementwise_rel, oracle_for, oracle_pops,
+                               pop_error)
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5        # up to a few hundred steps
+FP32_TOL_LONG = 1e-4   # 2000 steps of the small capillary
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _pair(geom, mp, precision="fp32"):
+    return lbm.Solver(geom, mp, precision), oracle_for(geom, mp)
+
+
+@pytest.mark.parametrize("nx,ny,seed", [(37, 23, 1), (64, 16, 2), (5, 4, 3),
+                                        (1, 9, 4), (130, 11, 5)])
+def test_random_state_steps(nx, ny, seed):
+    # Random solid, random two-phase blobs, random non-equilibrium
+    # populations and deposits close to the threshold: streaming, forces,
+    # collision, reaction and growth all active; sizes span several tiles
+    # with ragged edges, and lattices smaller than one tile.
+    geom = I.random_lattice(nx, ny, seed=seed, solid_fraction=0.15)
+    mp = I.ModelParams(g_ads=0.4, k_r=0.05, m_threshold=1.0)
+    s, o = _pair(geom, mp)
+    f, g = I.random_populations(geom, seed=seed + 100)
+    pops = np.concatenate([f.reshape(18, ny, nx), g])
+    rng = np.random.default_rng(seed + 200)
+    m0 = np.where(geom.solid == 0, 0.99 + 0.01 * rng.random((ny, nx)), 0.0)
+    s.set_populations(pops)
+    s.set_deposit(m0)
+    o.set_populations(f.astype(np.float64))
+    o.set_solute(g.astype(np.float64))
+    o.set_deposit(m0)
+    # the set/get round trip is exact
+    np.testing.assert_array_equal(s.populations(), pops * (geom.solid == 0))
+    for n in (1, 4):
+        s.step(n)
+        o.step(n)
+        np.testing.assert_array_equal(s.solid_mask(), o.solid())
+        assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+        np.testing.assert_allclose(s.deposit(), o.deposit(), rtol=1e-6,
+                                   atol=1e-7)
+        go = s.observables()[0]
+        led = o.ledger()
+        for k, key in enumerate(("ledger_a", "ledger_b", "ledger_c",
+                                 "ledger_m")):
+            assert go[key] == pytest.approx(led[k], rel=1e-5, abs=1e-6)
+    assert (s.solid_mask() != geom.solid).sum() > 0  # growth happened
+
+
+def test_small_capillary_2000_steps():
+    # The small configuration: 256 x 32 capillary, 30 degrees, tau 1.0,
+    # tau_D 0.8, c_in 1.0, k_r 1e-3, threshold 1.0, 2000 steps.
+    geom, mp, steps = I.config_small()
+    s, o = _pair(geom, mp)
+    fronts = []
+    for k in range(steps // 250):
+        s.step(250)
+        o.step(250)
+        go = s.observables()[0]
+        oo = A.lattice_observables(o)
+        fronts.append((go["front"], oo["front"]))
+        np.testing.assert_array_equal(s.solid_mask(), o.solid())
+        if np.isnan(oo["front"]):
+            assert np.isnan(go["front"])
+        else:
+            assert abs(go["front"] - oo["front"]) < 0.5
+        if o.step_count <= 500:
+            assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+    err = pop_error(s.populations(), oracle_pops(o))
+    print("small capillary: max population error / w_i = %.3g" % err)
+    assert err < FP32_TOL_LONG
+    go = s.observables()[0]
+    oo = A.lattice_observables(o)
+    assert go["closure_step"] == o.closure_step
+    for key in ("r_min", "r_ave", "r_h", "delta_e", "wetted_lower",
+                "wetted_upper", "closed"):
+        assert go[key] == pytest.approx(oo[key], abs=1e-9), key
+    for key in ("mass_a", "mass_b", "mass_c", "precip_mass", "ledger_a",
+                "ledger_b", "ledger_c", "ledger_m"):
+        assert go[key] == pytest.approx(oo[key], rel=1e-5, abs=1e-6), key
+    assert oo["ledger_a"] > 0  # growth happened within the 2000 steps
+
+
+def test_batch_matches_independent_lattices():
+    # Three capillaries of uneven size and constants in one handle (packed
+    # ragged layout, one launch per step) against three oracles.
+    members = [I.SweepMember(14, 90, 2e-2, 30.0, 1.0),
+               I.SweepMember(9, 61, 5e-3, 50.0, 1.3),
+               I.SweepMember(21, 120, 1e-2, 20.0, 0.8)]
+    geoms, mps = zip(*[I.sweep_lattice(m, x_res=16, x_out=8)
+                       for m in members])
+    mps = [I.ModelParams(**{**p.as_dict(), "m_threshold": 0.05}) for p in mps]
+    s = lbm.Solver(list(geoms), mps)
+    ors = [oracle_for(g, p) for g, p in zip(geoms, mps)]
+    s.step(300)
+    for o in ors:
+        o.step(300)
+    obs = s.observables()
+    for k, (g, o) in enumerate(zip(geoms, ors)):
+        np.testing.assert_array_equal(s.solid_mask(k), o.solid())
+        assert pop_error(s.populations(k), oracle_pops(o)) < FP32_TOL
+        oo = A.lattice_observables(o)
+        assert obs[k]["closure_step"] == o.closure_step
+        assert obs[k]["delta_e"] == oo["delta_e"]
+
+
+def test_checkpoint_continues_bit_for_bit(tmp_path):
+    geom, mp, _ = I.config_small()
+    a = lbm.Solver(geom, mp)
+    a.step(700)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(300)
+    b = lbm.Solver(geom, mp)
+    b.load(path)
+    assert b.step_count == 700
+    b.step(300)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    np.testing.assert_array_equal(a.deposit(), b.deposit())
+    np.testing.assert_array_equal(a.solid_mask(), b.solid_mask())
+
+
+def test_paper_scale_capillary_full_size():
+    # The paper-scale configuration at its full size (4096 x 128) in the
+    # launch configuration the benchmark times, for a stretch the oracle
+    # finishes in seconds, compared element by element.
+    geom, mp, _ = I.config_paper_scale(k_r=1e-3)
+    mp.m_threshold = 0.02   # growth inside the short stretch
+    s, o = _pair(geom, mp)
+    s.step(12)
+    o.step(12)
+    np.testing.assert_array_equal(s.solid_mask(), o.solid())
+    assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+    assert (o.solid() != geom.solid).sum() > 0
+
+
+def test_observables_match_oracle_definitions():
+    # Same state on both sides -> same observables (computed by the
+    # library's kernels vs the oracle's numpy definitions).
+    geom = I.capillary(120, 14, 24, 16)
+    mp = I.ModelParams(g_ads=I.G_ADS_30, k_r=2e-2, m_threshold=0.1, inlet=1)
+    s, o = _pair(geom, mp)
+    s.step(900)
+    o.step(900)
+    go = s.observables()[0]
+    oo = A.lattice_observables(o)
+    for key in ("r_min", "r_ave", "r_h", "delta_e", "wetted_lower",
+                "wetted_upper", "closed"):
+        assert go[key] == pytest.approx(oo[key], abs=1e-9), key
+    if np.isnan(oo["front"]):
+        assert np.isnan(go["front"])
+    else:
+        assert abs(go["front"] - oo["front"]) < 0.5
+    assert go["closure_step"] == o.closure_step
