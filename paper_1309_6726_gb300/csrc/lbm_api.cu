@@ -21,9 +21,13 @@ namespace lbmk {
 cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
                                int ty, bool half, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
-                            const CUtensorMap *mom_maps, int ntiles, int tx,
-                            int ty, bool half, int *err, cudaStream_t s);
+                            const CUtensorMap *mom_maps,
+                            const CUtensorMap *mask_maps, const int *sched,
+                            int nslots, int grid, int tx, int ty, bool half,
+                            int *err, cudaStream_t s);
+cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
 int tma_box_x(int tx, bool half);
+int tma_mask_box_x(int tx);
 __global__ void k_rest_state(const LatDesc *, int, const float *,
                              const float *, const float *, const uint8_t *,
                              float *);
@@ -82,6 +86,9 @@ struct lbm_handle {
     double *d_dep = nullptr;       // [ny][nx]
     CUtensorMap *d_maps = nullptr;     // [2 buffers][count] population maps
     CUtensorMap *d_mom_maps = nullptr; // [2 buffers][count] FP16 moment maps
+    CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
+    int *d_sched = nullptr;            // TMA kernel: tiles of each block
+    int sched_grid = 0, sched_slots = 0;
     int *d_err = nullptr;              // kernel error flags
     int cur = 0;
     int64_t steps = 0;
@@ -120,7 +127,8 @@ static void free_all(lbm_handle *h) {
                   h->d_pop[0], h->d_pop[1], h->d_mom[0], h->d_mom[1],
                   h->d_mask, h->d_m, h->d_col_fluid, h->d_wall0, h->d_st,
                   h->d_step, h->d_done, h->d_cols, h->d_obs, h->d_canon,
-                  h->d_dens, h->d_dep, h->d_maps, h->d_mom_maps, h->d_err};
+                  h->d_dens, h->d_dep, h->d_maps, h->d_mom_maps, h->d_mask_maps, h->d_err,
+                  h->d_sched};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->own) cudaStreamDestroy(h->own);
@@ -225,6 +233,30 @@ static bool make_maps(lbm_handle *h, std::string &why) {
             }
         }
     }
+    std::vector<CUtensorMap> mmaps(count);
+    for (int l = 0; l < count; ++l) {
+        const LatDesc &d = h->desc[l];
+        cuuint64_t dims[2] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny};
+        cuuint64_t strides[1] = {(cuuint64_t)d.pitch};
+        cuuint32_t box[2] = {(cuuint32_t)tma_mask_box_x(h->tx), (cuuint32_t)(h->ty + 4)};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(&mmaps[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                         h->d_mask + d.node_off, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            why = "cuTensorMapEncodeTiled failed for the mask, code " +
+                  std::to_string((int)r);
+            return false;
+        }
+    }
+    if (cudaMalloc(&h->d_mask_maps, mmaps.size() * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMemcpy(h->d_mask_maps, mmaps.data(), mmaps.size() * sizeof(CUtensorMap),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        why = "tensor map upload";
+        return false;
+    }
     if (cudaMalloc(&h->d_maps, maps.size() * sizeof(CUtensorMap)) != cudaSuccess ||
         cudaMemcpy(h->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -238,6 +270,58 @@ static bool make_maps(lbm_handle *h, std::string &why) {
         why = "tensor map upload";
         return false;
     }
+    return true;
+}
+
+// Tile schedule of the persistent TMA kernel: the tile columns ("strips")
+// of every lattice are dealt to the `grid` blocks, each to the block with
+// the least work so far (longest strips first); block b then walks its
+// strips top to bottom, its k-th tile at sched[b + k * grid] (-1 = done).
+static bool make_schedule(lbm_handle *h, std::string &why) {
+    int grid = 0;
+    cudaError_t e = grid_step_tma(h->tx, h->ty, h->half, &grid);
+    if (e != cudaSuccess || grid <= 0) {
+        why = std::string("TMA kernel setup: ") + cudaGetErrorString(e);
+        return false;
+    }
+    struct Strip { int lat, col, rows; };
+    std::vector<Strip> strips;
+    for (int l = 0; l < h->count; ++l) {
+        const LatDesc &d = h->desc[l];
+        const int rows = (d.ny + h->ty - 1) / h->ty;
+        for (int c = 0; c < d.tiles_x; ++c) strips.push_back({l, c, rows});
+    }
+    std::stable_sort(strips.begin(), strips.end(),
+                     [](const Strip &a, const Strip &b) { return a.rows > b.rows; });
+    std::vector<std::vector<int>> lists(grid);
+    std::vector<long long> load(grid, 0);
+    // blocks ordered by load with a simple binary heap
+    std::vector<int> heap(grid);
+    for (int b = 0; b < grid; ++b) heap[b] = b;
+    auto less = [&](int a, int b) { return load[a] > load[b] || (load[a] == load[b] && a > b); };
+    std::make_heap(heap.begin(), heap.end(), less);
+    for (const Strip &st : strips) {
+        std::pop_heap(heap.begin(), heap.end(), less);
+        const int b = heap.back();
+        const LatDesc &d = h->desc[st.lat];
+        for (int r = 0; r < st.rows; ++r)
+            lists[b].push_back(d.tile_base + r * d.tiles_x + st.col);
+        load[b] += st.rows;
+        std::push_heap(heap.begin(), heap.end(), less);
+    }
+    size_t slots = 0;
+    for (auto &v : lists) slots = std::max(slots, v.size());
+    std::vector<int> sched((size_t)grid * slots, -1);
+    for (int b = 0; b < grid; ++b)
+        for (size_t k = 0; k < lists[b].size(); ++k) sched[b + k * grid] = lists[b][k];
+    if (cudaMalloc(&h->d_sched, std::max<size_t>(sched.size(), 1) * sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(h->d_sched, sched.data(), sched.size() * sizeof(int),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        why = "schedule upload";
+        return false;
+    }
+    h->sched_grid = grid;
+    h->sched_slots = (int)slots;
     return true;
 }
 
@@ -256,7 +340,8 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
             return fail(nullptr, LBM_EINVAL,
                         "lattice " + std::to_string(l) +
                             ": need nx >= 1, ny >= 3 and all arrays");
-        if ((int64_t)G.nx * G.ny > (int64_t)1 << 31)
+        // 32-bit offsets inside a lattice: 22 planes of ny * pitch elements
+        if ((int64_t)NPOP * G.ny * ((G.nx + 31) / 32 * 32) >= ((int64_t)1 << 31))
             return fail(nullptr, LBM_EINVAL, "lattice too large");
         if (!(0 <= G.cap_x0 && G.cap_x0 < G.cap_x1 && G.cap_x1 <= G.nx))
             return fail(nullptr, LBM_EINVAL,
@@ -313,6 +398,8 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.c_in = (float)P.c_in;
         d.body_x = (float)P.body_force_x;
         d.m_th = P.m_threshold;
+        d.index = l;
+        d.pad_ = 0;
         h->max_nodes = std::max(h->max_nodes, (size_t)G.nx * G.ny);
     }
     h->ntiles = tiles;
@@ -418,7 +505,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     bad(cudaMemset(h->d_err, 0, sizeof(int)), "memset");
     if (st == LBM_OK && h->use_tma) {
         std::string why;
-        if (!make_maps(h, why)) {
+        if (!make_maps(h, why) || !make_schedule(h, why)) {
             g_create_err = why;
             st = LBM_ECUDA;
         }
@@ -509,7 +596,9 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
             h->use_tma
                 ? launch_step_tma(a, h->d_maps + h->cur * h->count,
                                   h->half ? h->d_mom_maps + h->cur * h->count : nullptr,
-                                  h->ntiles, h->tx, h->ty, h->half, h->d_err, h->stream)
+                                  h->d_mask_maps, h->d_sched, h->sched_slots,
+                                  h->sched_grid, h->tx, h->ty, h->half, h->d_err,
+                                  h->stream)
                 : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
         if (e == cudaErrorInvalidValue && k == 0)
             return fail(h, LBM_EINVAL, "unsupported tile shape");

@@ -66,8 +66,9 @@ struct MaskBits {
     }
 };
 
-// One lattice of the batch.
-struct LatDesc {
+// One lattice of the batch (128 bytes: the TMA step kernel bulk-copies it
+// into shared memory next to each tile).
+struct alignas(16) LatDesc {
     int32_t nx, ny, pitch, tiles_x;
     int32_t tile_base, cap_x0, cap_x1, inlet;
     int64_t node_off;   // first node of this lattice in mask / deposit
@@ -78,7 +79,10 @@ struct LatDesc {
     float tau_a, tau_b, inv_tau_a, inv_tau_b, inv_tau_d;
     float g_coh, g_ads, k_r, c_in, body_x;
     double m_th;
+    int32_t index;      // position of this lattice in the batch
+    int32_t pad_;
 };
+static_assert(sizeof(LatDesc) == 128, "LatDesc is copied as 128 bytes");
 
 struct LatState {
     double ledger[4];               // A, B, solute, deposit moved by growth

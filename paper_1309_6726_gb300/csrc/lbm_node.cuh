@@ -37,144 +37,151 @@ struct Store16 {
     using T = __half;
 };
 
-// D2Q9 BGK relaxation towards the equilibrium of (rho, ux, uy).  The rest
-// equilibrium is taken as rho minus the eight moving ones (the same value
-// in exact arithmetic): the FP32 weights sum to 1 + 7.45e-9, which would
-// otherwise create that much mass at every collision.
+// D2Q9 BGK relaxation towards the equilibrium of (rho, ux, uy),
+//   f_i^eq = w_i rho (1 + 3 e_i.u + 9/2 (e_i.u)^2 - 3/2 u.u),
+// evaluated pairwise: opposite directions share rho (1 - 3/2 u.u) +
+// 9/2 rho (e.u)^2 and differ in the sign of 3 rho e.u.  The rest
+// equilibrium is rho minus the eight moving ones (the same value in exact
+// arithmetic): the FP32 weights sum to 1 + 7.45e-9, which would otherwise
+// create that much mass at every collision.
 __device__ __forceinline__ void bgk9(float f[Q], float rho, float ux,
-                                     float uy, float inv_tau) {
-    const float uu = ux * ux + uy * uy;
-    float moving = 0.f;
+                                     float uy, float omega) {
+    const float a = rho * (1.0f - 1.5f * (ux * ux + uy * uy));
+    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+    const float up = ux + uy, um = ux - uy;
+    const float sx_ = a + r45 * ux * ux, sy_ = a + r45 * uy * uy;
+    const float sp = a + r45 * up * up, sm = a + r45 * um * um;
+    const float px = r3 * ux, py = r3 * uy, pp = r3 * up, pm = r3 * um;
+    const float w1 = wq(1), w5 = wq(5);
+    float feq[Q];
+    feq[1] = w1 * (sx_ + px);
+    feq[3] = w1 * (sx_ - px);
+    feq[2] = w1 * (sy_ + py);
+    feq[4] = w1 * (sy_ - py);
+    feq[5] = w5 * (sp + pp);   // (1, 1)
+    feq[7] = w5 * (sp - pp);   // (-1, -1)
+    feq[8] = w5 * (sm + pm);   // (1, -1)
+    feq[6] = w5 * (sm - pm);   // (-1, 1)
+    feq[0] = rho - (((feq[1] + feq[3]) + (feq[2] + feq[4])) +
+                    ((feq[5] + feq[7]) + (feq[6] + feq[8])));
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const float eu = (float)cx(i) * ux + (float)cy(i) * uy;
-        const float feq =
-            wq(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-        moving += feq;
-        f[i] = f[i] - (f[i] - feq) * inv_tau;
-    }
-    const float feq0 = rho - moving;
-    f[0] = f[0] - (f[0] - feq0) * inv_tau;
+    for (int i = 0; i < Q; ++i) f[i] = f[i] + omega * (feq[i] - f[i]);
+}
+
+// Density and momentum of 9 populations.
+__device__ __forceinline__ void moments9(const float f[Q], float &r,
+                                         float &jx, float &jy) {
+    r = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) +
+        ((f[5] + f[7]) + (f[6] + f[8]));
+    jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+    jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+}
+
+// sum_i w_i v(x + e_i) e_i for the eight neighbours v[1..8].
+__device__ __forceinline__ void stencil9(const float v[Q], float &sx_,
+                                         float &sy_) {
+    const float d1 = v[5] - v[7], d2 = v[8] - v[6];  // (1,1)-(-1,-1), (1,-1)-(-1,1)
+    sx_ = wq(1) * (v[1] - v[3]) + wq(5) * (d1 + d2);
+    sy_ = wq(1) * (v[2] - v[4]) + wq(5) * (d1 - d2);
 }
 
 template <class S>
-__device__ __forceinline__ void store9(typename S::T *__restrict__ fout,
-                                       __half *__restrict__ mout,
-                                       const LatDesc &d, int comp,
-                                       int64_t own, const float f[Q]) {
-    typename S::T *p = fout + d.pop_off + own;
+__device__ __forceinline__ void store9(typename S::T *__restrict__ p,
+                                       __half *__restrict__ mp, int plane,
+                                       const float f[Q]) {
     if constexpr (!S::kHalf) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) p[(comp * Q + i) * d.plane] = f[i];
+        for (int i = 0; i < Q; ++i) p[i * plane] = f[i];
     } else {
         float r = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) r += f[i];
         const __half rh = __float2half_rn(r);
         const float rt = __half2float(rh);
-        mout[d.mom_off + comp * d.plane + own] = rh;
+        *mp = rh;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            p[(comp * Q + i) * d.plane] = __float2half_rn(f[i] * (1.0f / wq(i)) - rt);
+            p[i * plane] = __float2half_rn(f[i] * (1.0f / wq(i)) - rt);
     }
 }
 
 template <class S>
-__device__ __forceinline__ void store4(typename S::T *__restrict__ fout,
-                                       __half *__restrict__ mout,
-                                       const LatDesc &d, int64_t own,
+__device__ __forceinline__ void store4(typename S::T *__restrict__ p,
+                                       __half *__restrict__ mp, int plane,
                                        const float g[QS]) {
-    typename S::T *p = fout + d.pop_off + own;
     if constexpr (!S::kHalf) {
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[(2 * Q + k) * d.plane] = g[k];
+        for (int k = 0; k < QS; ++k) p[k * plane] = g[k];
     } else {
-        const float c = g[0] + g[1] + g[2] + g[3];
+        const float c = (g[0] + g[2]) + (g[1] + g[3]);
         const __half ch = __float2half_rn(c);
         const float ct = __half2float(ch);
-        mout[d.mom_off + 2 * d.plane + own] = ch;
+        *mp = ch;
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[(2 * Q + k) * d.plane] = __float2half_rn(4.0f * g[k] - ct);
+        for (int k = 0; k < QS; ++k) p[k * plane] = __float2half_rn(4.0f * g[k] - ct);
     }
 }
 
 // Everything after the pull, for a node that is fluid in s_t.
 //   fA, fB, g: post-streaming populations of the node (g pulled already);
-//   rho_nb(c, i): density of component c at x + e_i (0 if solid in s_t);
-//   solid_nb(i): 1 if x + e_i is solid in s_t;  solid4(k) for D2Q4 links.
+//   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
+//   snb: bit i set if x + e_i is solid in s_t;  ns: solid D2Q4 links.
 // Returns true if the node reached the threshold in this step.
-template <class S, class RhoNb, class SolidNb, class Solid4>
+template <class S>
 __device__ __forceinline__ bool fluid_update(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx,
-    int64_t own, float fA[Q], float fB[Q], float g[QS], RhoNb rho_nb,
-    SolidNb solid_nb, Solid4 solid4) {
+    int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
+    const float rhoB_nb[Q], unsigned snb, int ns) {
     using T = typename S::T;
-    T *__restrict__ fout = static_cast<T *>(a.fout);
     // ---- moments ----------------------------------------------------------
-    float rA = 0.f, rB = 0.f, jAx = 0.f, jAy = 0.f, jBx = 0.f, jBy = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        rA += fA[i];
-        rB += fB[i];
-        jAx += (float)cx(i) * fA[i];
-        jAy += (float)cy(i) * fA[i];
-        jBx += (float)cx(i) * fB[i];
-        jBy += (float)cy(i) * fB[i];
-    }
+    float rA, jAx, jAy, rB, jBx, jBy;
+    moments9(fA, rA, jAx, jAy);
+    moments9(fB, rB, jBx, jBy);
     // ---- Martys-Chen forces ----------------------------------------------
-    float cAx = 0.f, cAy = 0.f, cBx = 0.f, cBy = 0.f, adx = 0.f, ady = 0.f;
+    float cAx, cAy, cBx, cBy, adx, ady;
+    stencil9(rhoB_nb, cAx, cAy);  // A feels B
+    stencil9(rhoA_nb, cBx, cBy);  // B feels A
+    {
+        float sv[Q];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const float rbn = rho_nb(1, i);
-        const float ran = rho_nb(0, i);
-        const float sn = solid_nb(i) ? 1.f : 0.f;
-        cAx += wq(i) * rbn * (float)cx(i);
-        cAy += wq(i) * rbn * (float)cy(i);
-        cBx += wq(i) * ran * (float)cx(i);
-        cBy += wq(i) * ran * (float)cy(i);
-        adx += wq(i) * sn * (float)cx(i);
-        ady += wq(i) * sn * (float)cy(i);
+        for (int i = 1; i < Q; ++i) sv[i] = ((snb >> i) & 1u) ? 1.f : 0.f;
+        stencil9(sv, adx, ady);
     }
     // G_ads,A = -g_ads, G_ads,B = +g_ads
-    const float FAx = -d.g_coh * rA * cAx + d.g_ads * rA * adx + rA * d.body_x;
-    const float FAy = -d.g_coh * rA * cAy + d.g_ads * rA * ady;
-    const float FBx = -d.g_coh * rB * cBx - d.g_ads * rB * adx + rB * d.body_x;
-    const float FBy = -d.g_coh * rB * cBy - d.g_ads * rB * ady;
+    const float FAx = rA * (d.g_ads * adx - d.g_coh * cAx + d.body_x);
+    const float FAy = rA * (d.g_ads * ady - d.g_coh * cAy);
+    const float FBx = rB * (-d.g_ads * adx - d.g_coh * cBx + d.body_x);
+    const float FBy = rB * (-d.g_ads * ady - d.g_coh * cBy);
     // ---- Shan-Chen shift and BGK -----------------------------------------
     const float den = rA * d.inv_tau_a + rB * d.inv_tau_b;
-    const float upx = den > 0.f ? (jAx * d.inv_tau_a + jBx * d.inv_tau_b) / den : 0.f;
-    const float upy = den > 0.f ? (jAy * d.inv_tau_a + jBy * d.inv_tau_b) / den : 0.f;
-    float uAx = upx, uAy = upy, uBx = upx, uBy = upy;
-    if (rA > 1e-12f) { uAx += d.tau_a * FAx / rA; uAy += d.tau_a * FAy / rA; }
-    if (rB > 1e-12f) { uBx += d.tau_b * FBx / rB; uBy += d.tau_b * FBy / rB; }
-    bgk9(fA, rA, uAx, uAy, d.inv_tau_a);
-    bgk9(fB, rB, uBx, uBy, d.inv_tau_b);
+    const float iden = den > 0.f ? __frcp_rn(den) : 0.f;
+    const float upx = (jAx * d.inv_tau_a + jBx * d.inv_tau_b) * iden;
+    const float upy = (jAy * d.inv_tau_a + jBy * d.inv_tau_b) * iden;
+    const float sA = rA > 1e-12f ? d.tau_a * __frcp_rn(rA) : 0.f;
+    const float sB = rB > 1e-12f ? d.tau_b * __frcp_rn(rB) : 0.f;
+    bgk9(fA, rA, upx + sA * FAx, upy + sA * FAy, d.inv_tau_a);
+    bgk9(fB, rB, upx + sB * FBx, upy + sB * FBy, d.inv_tau_b);
     // ---- solute ----------------------------------------------------------
     const float rt = rA + rB;
-    const float ux = rt > 0.f ? (jAx + jBx + 0.5f * (FAx + FBx)) / rt : 0.f;
-    const float uy = rt > 0.f ? (jAy + jBy + 0.5f * (FAy + FBy)) / rt : 0.f;
-    if (d.inlet && gx == 0) {
+    const float irt = rt > 0.f ? __frcp_rn(rt) : 0.f;
+    const float ux = ((jAx + jBx) + 0.5f * (FAx + FBx)) * irt;
+    const float uy = ((jAy + jBy) + 0.5f * (FAy + FBy)) * irt;
+    {
+        const bool inl = d.inlet && gx == 0;
+        const float c = inl ? d.c_in : (g[0] + g[2]) + (g[1] + g[3]);
+        const float q = 0.25f * c, hx2 = 0.5f * c * ux, hy2 = 0.5f * c * uy;
+        const float geq[QS] = {q + hx2, q + hy2, q - hx2, q - hy2};
+        const float om = inl ? 1.0f : d.inv_tau_d;
 #pragma unroll
-        for (int k = 0; k < QS; ++k)
-            g[k] = 0.25f * d.c_in * (1.0f + 2.0f * ((float)sx(k) * ux + (float)sy(k) * uy));
-    } else {
-        const float c = g[0] + g[1] + g[2] + g[3];
-#pragma unroll
-        for (int k = 0; k < QS; ++k) {
-            const float geq = 0.25f * c * (1.0f + 2.0f * ((float)sx(k) * ux + (float)sy(k) * uy));
-            g[k] = g[k] - (g[k] - geq) * d.inv_tau_d;
-        }
+        for (int k = 0; k < QS; ++k) g[k] = g[k] + om * (geq[k] - g[k]);
     }
     // ---- surface reaction, deposit, threshold ----------------------------
-    int ns = 0;
-#pragma unroll
-    for (int k = 0; k < QS; ++k) ns += solid4(k) ? 1 : 0;
     bool flagged = false;
     if (ns > 0 && rA > rB) {
         // fraction of the solute consumed, k_r n_s (capped at all of it);
         // applied as g - g * lost rather than g * (1 - lost) so that
         // rounding 1 - lost does not bias the small consumption
-        const float cs = g[0] + g[1] + g[2] + g[3];
+        const float cs = (g[0] + g[2]) + (g[1] + g[3]);
         const float lost = fminf(1.0f, d.k_r * (float)ns);
 #pragma unroll
         for (int k = 0; k < QS; ++k) g[k] -= g[k] * lost;
@@ -191,9 +198,12 @@ __device__ __forceinline__ bool fluid_update(
         }
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
-    store9<S>(fout, a.mout, d, 0, own, fA);
-    store9<S>(fout, a.mout, d, 1, own, fB);
-    store4<S>(fout, a.mout, d, own, g);
+    T *p = static_cast<T *>(a.fout) + d.pop_off + own;
+    const int pl = (int)d.plane;
+    __half *mp = S::kHalf ? a.mout + d.mom_off + own : nullptr;
+    store9<S>(p, mp, pl, fA);
+    store9<S>(p + Q * pl, S::kHalf ? mp + pl : nullptr, pl, fB);
+    store4<S>(p + 2 * Q * pl, S::kHalf ? mp + 2 * pl : nullptr, pl, g);
     return flagged;
 }
 
@@ -201,7 +211,7 @@ __device__ __forceinline__ bool fluid_update(
 // deposit go to the lattice ledger.
 __device__ __forceinline__ void retire_node(const StepArgs &a,
                                             const LatDesc &d, int l,
-                                            int64_t own, const float fA[Q],
+                                            int own, const float fA[Q],
                                             const float fB[Q],
                                             const float g[QS]) {
     double ra = 0, rb = 0;

@@ -178,12 +178,15 @@ __global__ void __launch_bounds__(TX *TY)
     __syncthreads();
 
     if (active) {
-        const int64_t own = (int64_t)gy * d.pitch + gx;
+        const int own = gy * d.pitch + gx;
         const int hy = ly + 2, hx = lx + 2;
         unsigned bb4 = 0;
+        int ns = 0;
 #pragma unroll
-        for (int k = 0; k < QS; ++k)
+        for (int k = 0; k < QS; ++k) {
             if (smask[hy - sy(k)][hx - sx(k)] & mb.pull) bb4 |= 1u << k;
+            if (smask[hy + sy(k)][hx + sx(k)] & mb.force) ++ns;
+        }
         if (s_own & mb.force) {
             const uint8_t nb = s_own | mb.next;
             if (own_pull_fluid) {
@@ -193,13 +196,17 @@ __global__ void __launch_bounds__(TX *TY)
             }
             if (nb != s_own) mask[own] = nb;
         } else {
-            float g[QS];
+            float g[QS], rAn[Q], rBn[Q];
+            unsigned snb = 0;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                rAn[i] = srho[0][ly + 1 + cy(i)][lx + 1 + cx(i)];
+                rBn[i] = srho[1][ly + 1 + cy(i)][lx + 1 + cx(i)];
+                if (smask[hy + cy(i)][hx + cx(i)] & mb.force) snb |= 1u << i;
+            }
             pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
-            const bool flagged = fluid_update<S>(
-                a, d, l, t, gx, own, fA, fB, g,
-                [&](int c, int i) { return srho[c][ly + 1 + cy(i)][lx + 1 + cx(i)]; },
-                [&](int i) { return (smask[hy + cy(i)][hx + cx(i)] & mb.force) != 0; },
-                [&](int k) { return (smask[hy + sy(k)][hx + sx(k)] & mb.force) != 0; });
+            const bool flagged = fluid_update<S>(a, d, l, t, gx, own, fA, fB, g,
+                                                 rAn, rBn, snb, ns);
             if (flagged) mask[own] = s_own | mb.next;
         }
     }

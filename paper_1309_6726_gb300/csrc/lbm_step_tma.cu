@@ -87,6 +87,25 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map,
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
+                                            int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::"
+        "bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src,
+                                          unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---- tile geometry -----------------------------------------------------------
 
 template <class S, int TX_, int TY_>
@@ -94,30 +113,38 @@ struct TmaTile {
     using T = typename S::T;
     static constexpr int TX = TX_, TY = TY_;
     static constexpr int NT = TX * TY;
+    static constexpr int NW = NT / 32;            // warps
     static constexpr int XO = S::kHalf ? 8 : 4;  // halo columns copied
     static constexpr int BX = TX + 2 * XO;        // box width
     static constexpr int BY = TY + 4;             // box height (halo 2)
     static constexpr int PL = BX * BY;            // elements per plane
+    static constexpr int MXO = 16;                // mask box: 16-byte aligned
+    static constexpr int MBX = TX + 2 * MXO;
     static constexpr int POP_BYTES = NPOP * PL * (int)sizeof(T);
     static constexpr int MOM_BYTES = S::kHalf ? NMOM * PL * 2 : 0;
-    static constexpr int STAGE = ((POP_BYTES + MOM_BYTES) + 127) / 128 * 128;
-    static constexpr int HX = TX + 4, HY = TY + 4;  // mask halo, radius 2
+    static constexpr int MASK_BYTES = (MBX * BY + 127) / 128 * 128;
+    static constexpr int STAGE =
+        ((POP_BYTES + MOM_BYTES + 127) / 128 * 128) + MASK_BYTES;
+    static constexpr int MASK_OFF = STAGE - MASK_BYTES;  // within a stage
+    static constexpr int TX_BYTES = POP_BYTES + MOM_BYTES + MBX * BY + 128;
     static constexpr int RX = TX + 2, RY = TY + 2;  // density frame
     static constexpr int NRING = 2 * RX + 2 * TY;
-    static constexpr int MASK_BYTES = (HX * HY + 127) / 128 * 128;
-    static constexpr int RHO_BYTES = (2 * RX * RY * 4 + 127) / 128 * 128;
-    static constexpr int SMEM = 2 * STAGE + MASK_BYTES + RHO_BYTES + 128;
-    static_assert(POP_BYTES % 128 == 0, "stage alignment");
+    static constexpr int RHO_BYTES = 2 * RX * RY * 4;
+    static constexpr int DESC_OFF = 2 * STAGE;                 // 3 x 128
+    static constexpr int RHO_OFF = DESC_OFF + 3 * 128;         // 2 frames
+    static constexpr int BAR_OFF = RHO_OFF + 2 * ((RHO_BYTES + 127) / 128 * 128);
+    static constexpr int SMEM = BAR_OFF + 128;
+    static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0, "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
+    static_assert(NRING <= NT && NRING / NW < 32, "ring spread");
 };
 
 // The 9 populations of component `comp` pulled into the node at stage cell
-// (yy, xx), from shared memory.
+// `c`, from shared memory (bb: bounce-back bits).
 template <class S, class TT>
 __device__ __forceinline__ void spull9(const typename S::T *tile,
-                                       const __half *mom, int comp, int yy,
-                                       int xx, unsigned bb, float f[Q]) {
-    const int c = yy * TT::BX + xx;
+                                       const __half *mom, int comp, int c,
+                                       unsigned bb, float f[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool b = (bb >> i) & 1u;
@@ -134,9 +161,8 @@ __device__ __forceinline__ void spull9(const typename S::T *tile,
 
 template <class S, class TT>
 __device__ __forceinline__ void spull4(const typename S::T *tile,
-                                       const __half *mom, int yy, int xx,
-                                       unsigned bb4, float g[QS]) {
-    const int c = yy * TT::BX + xx;
+                                       const __half *mom, int c, unsigned bb4,
+                                       float g[QS]) {
 #pragma unroll
     for (int k = 0; k < QS; ++k) {
         const bool b = (bb4 >> k) & 1u;
@@ -151,10 +177,24 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
     }
 }
 
+// Mask bits around the node at mask-box cell mc: bit i of the result is set
+// when the node at mc + e_i (sign = +1) or mc - e_i (sign = -1) has `bit`.
+template <class TT, int SIGN>
+__device__ __forceinline__ unsigned nb_bits(const uint8_t *sm, int mc,
+                                            uint8_t bit) {
+    unsigned r = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (sm[mc + SIGN * (cy(i) * TT::MBX + cx(i))] & bit) r |= 1u << i;
+    return r;
+}
+
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY)
     k_step_tma(StepArgs a, const CUtensorMap *__restrict__ pop_maps,
-               const CUtensorMap *__restrict__ mom_maps, int ntiles,
+               const CUtensorMap *__restrict__ mom_maps,
+               const CUtensorMap *__restrict__ mask_maps,
+               const int *__restrict__ sched, int nslots,
                int *__restrict__ err) {
     using TT = TmaTile<S, TX, TY>;
     using T = typename S::T;
@@ -163,237 +203,270 @@ __global__ void __launch_bounds__(TX *TY)
     auto stage_mom = [&](int s) {
         return reinterpret_cast<__half *>(smem + s * TT::STAGE + TT::POP_BYTES);
     };
-    uint8_t(*smask)[TT::HX] =
-        reinterpret_cast<uint8_t(*)[TT::HX]>(smem + 2 * TT::STAGE);
-    float(*srho)[TT::RY][TT::RX] = reinterpret_cast<float(*)[TT::RY][TT::RX]>(
-        smem + 2 * TT::STAGE + TT::MASK_BYTES);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TT::STAGE +
-                                                 TT::MASK_BYTES + TT::RHO_BYTES);
+    auto stage_mask = [&](int s) { return smem + s * TT::STAGE + TT::MASK_OFF; };
+    auto sdesc = [&](int slot) {
+        return reinterpret_cast<LatDesc *>(smem + TT::DESC_OFF + 128 * slot);
+    };
+    auto srho = [&](int s) {
+        return reinterpret_cast<float *>(smem + TT::RHO_OFF +
+                                         s * ((TT::RHO_BYTES + 127) / 128 * 128));
+    };
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TT::BAR_OFF);
     long long *s_t = reinterpret_cast<long long *>(bar + 2);
+    int *s_tile = reinterpret_cast<int *>(bar + 3);  // tile of each desc slot
+
+    // This block's tiles: sched[blockIdx.x + k * gridDim.x], k = 0, 1, ...,
+    // until the first -1; consecutive entries walk down one tile column of a
+    // lattice, so the halo rows a tile copies were copied by the previous
+    // tile of the same block and come from L2.
+    auto sched_at = [&](int k) {
+        return k < nslots ? sched[blockIdx.x + (size_t)k * gridDim.x] : -1;
+    };
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const T *__restrict__ fin = static_cast<const T *>(a.fin);
+
+    // Copies tile `tile` into stage s and its lattice descriptor into `slot`.
+    auto issue = [&](int tile, int s, int slot) {
+        const int l = a.tile_lat[tile];
+        const LatDesc *gd = a.desc + l;
+        const int local = tile - gd->tile_base;
+        const int tiles_x = gd->tiles_x;
+        const int x0 = (local % tiles_x) * TX;
+        const int y0 = (local / tiles_x) * TY - 2;
+        s_tile[slot] = tile;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[s], TT::TX_BYTES);
+        bulk_load(sdesc(slot), gd, 128, &bar[s]);
+        tma_load_3d(stage_pop(s), &pop_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
+        if constexpr (S::kHalf)
+            tma_load_3d(stage_mom(s), &mom_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
+        tma_load_2d(stage_mask(s), &mask_maps[l], x0 - TT::MXO, y0, &bar[s]);
+    };
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         *s_t = *(volatile long long *)a.step;
+        const int t0 = sched_at(0), t1 = sched_at(1);
+        if (t0 >= 0) issue(t0, 0, 0);
+        if (t0 >= 0 && t1 >= 0) issue(t1, 1, 1);
     }
     __syncthreads();
     const long long t = *s_t;
     const MaskBits mb(t);
 
-    auto issue = [&](int tile, int s) {
-        const int l = a.tile_lat[tile];
-        const LatDesc &dd = a.desc[l];
-        const int local = tile - dd.tile_base;
-        const int x0 = (local % dd.tiles_x) * TX - TT::XO;
-        const int y0 = (local / dd.tiles_x) * TY - 2;
-        fence_proxy_async();
-        mbar_expect_tx(&bar[s], TT::POP_BYTES + TT::MOM_BYTES);
-        tma_load_3d(stage_pop(s), &pop_maps[l], x0, y0, 0, &bar[s]);
-        if constexpr (S::kHalf)
-            tma_load_3d(stage_mom(s), &mom_maps[l], x0, y0, 0, &bar[s]);
-    };
-
-    int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) issue(tile, 0);
     unsigned parity = 0u;  // bit s: phase parity of stage s
-    bool failed = false;
-    for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    for (int k = 0; sched_at(k) >= 0; ++k) {
         const int s = k & 1;
-        const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) issue(next, s ^ 1);
-
-        const int l = a.tile_lat[tile];
-        const LatDesc d = a.desc[l];
+        const int slot = k % 3;
+        const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
+        parity ^= 1u << s;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(err, 1);
+                if (sched_at(k + 1) >= 0)
+                    mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
+            }
+            break;
+        }
+        const int tile = s_tile[slot];
+        const LatDesc &d = *sdesc(slot);
+        const int l = d.index;
         const int nx = d.nx, ny = d.ny;
         const int local = tile - d.tile_base;
         const int tx0 = (local % d.tiles_x) * TX;
         const int ty0 = (local / d.tiles_x) * TY;
         const bool edge = tx0 < 2 || ty0 < 2 || tx0 + TX + 2 > nx ||
                           ty0 + TY + 2 > ny;
-        uint8_t *__restrict__ mask = a.mask + d.node_off;
-
-        // mask halo (plain loads; overlaps the copy in flight)
-        for (int e = tid; e < TT::HY * TT::HX; e += TT::NT) {
-            const int hy = e / TT::HX, hx = e - hy * TT::HX;
-            int gy = ty0 - 2 + hy, gx = tx0 - 2 + hx;
-            if (edge) {
-                gy = wrapg(gy, ny);
-                gx = wrapg(gx, nx);
-            }
-            smask[hy][hx] = mask[(int64_t)gy * d.pitch + gx];
-        }
-
-        // wait for this tile's copy (bounded; the decision is block-uniform)
-        const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
-        parity ^= 1u << s;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            if (tid == 0) {
-                atomicOr(err, 1);
-                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
-            }
-            break;
-        }
         T *tp = stage_pop(s);
         __half *tm = stage_mom(s);
+        uint8_t *sm = stage_mask(s);
 
-        // periodic images of halo cells outside the lattice
+        // periodic images of halo cells outside the lattice (the copies
+        // filled them with zeros); one thread per such cell, all planes;
+        // cells spread over the warps
+        // rows / columns of the tile that hold lattice nodes; the frame
+        // needs one more around them and the pulls of the frame one more
+        const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
         if (edge) {
             const T *__restrict__ src = fin + d.pop_off;
-            constexpr int NPL = NPOP + (S::kHalf ? NMOM : 0);
-            constexpr int CW = TX + 4;  // columns needed: x0 - 2 .. x0 + TX + 1
-            for (int e = tid; e < TT::BY * CW * NPL; e += TT::NT) {
-                const int q = e / (TT::BY * CW);
-                const int r = e - q * (TT::BY * CW);
-                const int yy = r / CW;
-                const int xx = r - yy * CW + TT::XO - 2;
-                const int gy = ty0 - 2 + yy, gx = tx0 - TT::XO + xx;
+            const uint8_t *__restrict__ msrc = a.mask + d.node_off;
+            const int CW = m_act + 4;   // columns read: x0 - 2 .. x0 + m_act + 1
+            const int RH = n_act + 4;   // rows read: y0 - 2 .. y0 + n_act + 1
+            for (int j = 0; j * TT::NT < RH * CW; ++j) {
+                const int e = j * TT::NT + lane * TT::NW + warp;
+                if (e >= RH * CW) continue;
+                const int yy = e / CW;
+                const int xc = e - yy * CW - 2;  // column relative to x0
+                const int gy = ty0 - 2 + yy, gx = tx0 + xc;
                 if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-                const int64_t g = (int64_t)wrapg(gy, ny) * d.pitch + wrapg(gx, nx);
-                if (q < NPOP) {
-                    tp[q * TT::PL + yy * TT::BX + xx] = src[q * d.plane + g];
-                } else if constexpr (S::kHalf) {
-                    tm[(q - NPOP) * TT::PL + yy * TT::BX + xx] =
-                        a.min_[d.mom_off + (q - NPOP) * d.plane + g];
+                const int g = wrapg(gy, ny) * d.pitch + wrapg(gx, nx);
+                const int cell = yy * TT::BX + xc + TT::XO;
+#pragma unroll 2
+                for (int q = 0; q < NPOP; ++q)
+                    tp[q * TT::PL + cell] = src[(int64_t)q * d.plane + g];
+                if constexpr (S::kHalf) {
+#pragma unroll
+                    for (int q = 0; q < NMOM; ++q)
+                        tm[q * TT::PL + cell] = a.min_[d.mom_off + (int64_t)q * d.plane + g];
                 }
+                sm[yy * TT::MBX + xc + TT::MXO] = msrc[g];
             }
+            __syncthreads();
         }
-        __syncthreads();
 
-        // own node: pull and density
+        // own node: mask bits, pull, density
         const int lx = tid % TX, ly = tid / TX;
         const int x = tx0 + lx, y = ty0 + ly;
         const bool active = (x < nx) && (y < ny);
-        const int yy = ly + 2, xx = lx + TT::XO;
-        const int hy = ly + 2, hx = lx + 2;
-        const uint8_t s_own = smask[hy][hx];
+        const bool in_frame = lx <= m_act && ly <= n_act;  // neighbour of a node
+        const int pc = (ly + 2) * TT::BX + lx + TT::XO;    // stage cell
+        const int mc = (ly + 2) * TT::MBX + lx + TT::MXO;  // mask cell
+        const uint8_t s_own = in_frame ? sm[mc] : (uint8_t)0xFF;
         const bool own_pull_fluid = !(s_own & mb.pull);
-        float fA[Q], fB[Q];
+        const unsigned bb = nb_bits<TT, -1>(sm, mc, mb.pull);   // sources solid
+        const unsigned snb = nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
+        float fA[Q], fB[Q], g[QS];
+        float *fr = srho(s);
         {
             float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
-                unsigned bb = 0;
-#pragma unroll
-                for (int i = 1; i < Q; ++i)
-                    if (smask[hy - cy(i)][hx - cx(i)] & mb.pull) bb |= 1u << i;
-                spull9<S, TT>(tp, tm, 0, yy, xx, bb, fA);
-                spull9<S, TT>(tp, tm, 1, yy, xx, bb, fB);
+                spull9<S, TT>(tp, tm, 0, pc, bb, fA);
+                spull9<S, TT>(tp, tm, 1, pc, bb, fB);
+                spull4<S, TT>(tp, tm, pc, (bb >> 1) & 0xFu, g);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
             }
             const bool force_solid = s_own & mb.force;
-            srho[0][ly + 1][lx + 1] = force_solid ? 0.f : ra;
-            srho[1][ly + 1][lx + 1] = force_solid ? 0.f : rb;
+            fr[(ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : ra;
+            fr[TT::RX * TT::RY + (ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : rb;
         }
-        // ring of the density frame
-        for (int r = tid; r < TT::NRING; r += TT::NT) {
-            int ry, rx;
-            if (r < TT::RX) { ry = 0; rx = r; }
-            else if (r < 2 * TT::RX) { ry = TT::RY - 1; rx = r - TT::RX; }
-            else if (r < 2 * TT::RX + TY) { ry = 1 + r - 2 * TT::RX; rx = 0; }
-            else { ry = 1 + r - 2 * TT::RX - TY; rx = TT::RX - 1; }
-            const uint8_t sr = smask[ry + 1][rx + 1];
-            float ra = 0.f, rb = 0.f;
-            if (!(sr & mb.force)) {
-                unsigned bb = 0;
+        // ring of the density frame, spread over the warps
+        {
+            const int r = lane * TT::NW + warp;
+            if (r < TT::NRING) {
+                int ry, rx;
+                if (r < TT::RX) { ry = 0; rx = r; }
+                else if (r < 2 * TT::RX) { ry = TT::RY - 1; rx = r - TT::RX; }
+                else if (r < 2 * TT::RX + TY) { ry = 1 + r - 2 * TT::RX; rx = 0; }
+                else { ry = 1 + r - 2 * TT::RX - TY; rx = TT::RX - 1; }
+                const int rmc = (ry + 1) * TT::MBX + rx - 1 + TT::MXO;
+                const int rpc = (ry + 1) * TT::BX + rx - 1 + TT::XO;
+                float ra = 0.f, rb = 0.f;
+                if (!(sm[rmc] & mb.force)) {
+                    const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
+                    float f[Q];
+                    spull9<S, TT>(tp, tm, 0, rpc, rbb, f);
 #pragma unroll
-                for (int i = 1; i < Q; ++i)
-                    if (smask[ry + 1 - cy(i)][rx + 1 - cx(i)] & mb.pull) bb |= 1u << i;
-                float f[Q];
-                spull9<S, TT>(tp, tm, 0, ry + 1, rx + TT::XO - 1, bb, f);
+                    for (int i = 0; i < Q; ++i) ra += f[i];
+                    spull9<S, TT>(tp, tm, 1, rpc, rbb, f);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) ra += f[i];
-                spull9<S, TT>(tp, tm, 1, ry + 1, rx + TT::XO - 1, bb, f);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) rb += f[i];
+                    for (int i = 0; i < Q; ++i) rb += f[i];
+                }
+                fr[ry * TT::RX + rx] = ra;
+                fr[TT::RX * TT::RY + ry * TT::RX + rx] = rb;
             }
-            srho[0][ry][rx] = ra;
-            srho[1][ry][rx] = rb;
         }
+        fence_proxy_async();
         __syncthreads();
+        // stage s is free: start the copy of the tile after next into it
+        if (tid == 0) {
+            const int t2 = sched_at(k + 2);
+            if (t2 >= 0) issue(t2, s, (k + 2) % 3);
+        }
 
         if (active) {
-            const int64_t own = (int64_t)y * d.pitch + x;
-            unsigned bb4 = 0;
-#pragma unroll
-            for (int k4 = 0; k4 < QS; ++k4)
-                if (smask[hy - sy(k4)][hx - sx(k4)] & mb.pull) bb4 |= 1u << k4;
+            const int own = y * d.pitch + x;
             if (s_own & mb.force) {
+                if (own_pull_fluid) retire_node(a, d, l, own, fA, fB, g);
                 const uint8_t nb = s_own | mb.next;
-                if (own_pull_fluid) {
-                    float g[QS];
-                    spull4<S, TT>(tp, tm, yy, xx, bb4, g);
-                    retire_node(a, d, l, own, fA, fB, g);
-                }
-                if (nb != s_own) mask[own] = nb;
+                if (nb != s_own) a.mask[d.node_off + own] = nb;
             } else {
-                float g[QS];
-                spull4<S, TT>(tp, tm, yy, xx, bb4, g);
-                const bool flagged = fluid_update<S>(
-                    a, d, l, t, x, own, fA, fB, g,
-                    [&](int c, int i) { return srho[c][ly + 1 + cy(i)][lx + 1 + cx(i)]; },
-                    [&](int i) { return (smask[hy + cy(i)][hx + cx(i)] & mb.force) != 0; },
-                    [&](int k4) { return (smask[hy + sy(k4)][hx + sx(k4)] & mb.force) != 0; });
-                if (flagged) mask[own] = s_own | mb.next;
+                float rAn[Q], rBn[Q];
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int fc = (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i);
+                    rAn[i] = fr[fc];
+                    rBn[i] = fr[TT::RX * TT::RY + fc];
+                }
+                const int ns = __popc(snb & 0x1Eu);
+                const bool flagged = fluid_update<S>(a, d, l, t, x, own, fA, fB, g,
+                                                     rAn, rBn, snb, ns);
+                if (flagged) a.mask[d.node_off + own] = s_own | mb.next;
             }
         }
-        // stage s, the mask halo and the density frame are reused next
-        __syncthreads();
     }
-    (void)failed;
     finish_launch(a, t);
 }
 
 // ---- host side ---------------------------------------------------------------
 
 template <class S, int TX, int TY>
-static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
-                                const CUtensorMap *mom_maps, int ntiles,
-                                int *err, cudaStream_t s) {
+static cudaError_t grid_tma_t(int *grid) {
     using TT = TmaTile<S, TX, TY>;
-    static int grid = 0;
-    if (grid == 0) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k_step_tma<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            TT::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, k_step_tma<S, TX, TY>, TX * TY, TT::SMEM);
-        if (e != cudaSuccess) return e;
-        grid = sms * (per > 0 ? per : 1);
-    }
-    const int g = ntiles < grid ? ntiles : grid;
-    k_step_tma<S, TX, TY><<<g, TX * TY, TT::SMEM, s>>>(a, pop_maps, mom_maps,
-                                                       ntiles, err);
+    cudaError_t e = cudaFuncSetAttribute(
+        k_step_tma<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        TT::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tma<S, TX, TY>,
+                                                      TX * TY, TT::SMEM);
+    if (e != cudaSuccess) return e;
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
+}
+
+template <class S, int TX, int TY>
+static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
+                                const CUtensorMap *mom_maps,
+                                const CUtensorMap *mask_maps, const int *sched,
+                                int nslots, int grid, int *err, cudaStream_t s) {
+    using TT = TmaTile<S, TX, TY>;
+    k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(
+        a, pop_maps, mom_maps, mask_maps, sched, nslots, err);
     return cudaGetLastError();
 }
 
+#define LBM_TMA_SHAPES(M) M(32, 8) M(32, 4) M(64, 4) M(32, 16) M(64, 8)
+
+// Persistent grid of the TMA step kernel for a tile shape (also sets its
+// shared-memory limit); 0 on an unsupported shape.
+cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
+    *grid = 0;
+#define LBM_TMA_GRID(X, Y)                                                   \
+    if (tx == X && ty == Y)                                                  \
+        return half ? grid_tma_t<Store16, X, Y>(grid) : grid_tma_t<Store32, X, Y>(grid);
+    LBM_TMA_SHAPES(LBM_TMA_GRID)
+#undef LBM_TMA_GRID
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
-                            const CUtensorMap *mom_maps, int ntiles, int tx,
-                            int ty, bool half, int *err, cudaStream_t s) {
+                            const CUtensorMap *mom_maps,
+                            const CUtensorMap *mask_maps, const int *sched,
+                            int nslots, int grid, int tx, int ty, bool half,
+                            int *err, cudaStream_t s) {
 #define LBM_TMA_CASE(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
         return half ? launch_tma_t<Store16, X, Y>(a, pop_maps, mom_maps,     \
-                                                  ntiles, err, s)            \
+                                                  mask_maps, sched, nslots,  \
+                                                  grid, err, s)              \
                     : launch_tma_t<Store32, X, Y>(a, pop_maps, mom_maps,     \
-                                                  ntiles, err, s);
-    LBM_TMA_CASE(32, 8)
-    LBM_TMA_CASE(32, 4)
-    LBM_TMA_CASE(64, 4)
-    LBM_TMA_CASE(32, 16)
-    LBM_TMA_CASE(64, 8)
+                                                  mask_maps, sched, nslots,  \
+                                                  grid, err, s);
+    LBM_TMA_SHAPES(LBM_TMA_CASE)
 #undef LBM_TMA_CASE
     return cudaErrorInvalidValue;
 }
 
-// Tensor map geometry must match TmaTile: box (TX + 2 XO) x (TY + 4) x planes.
+// Tensor map geometry must match TmaTile: box (TX + 2 XO) x (TY + 4) x
+// planes for populations and moments, (TX + 32) x (TY + 4) for the mask.
 int tma_box_x(int tx, bool half) { return tx + 2 * (half ? 8 : 4); }
+int tma_mask_box_x(int tx) { return tx + 32; }
 
 }  // namespace lbmk

@@ -4,10 +4,11 @@ the same seeded inputs.
 Tolerances.  The kernels compute in FP32 and store FP32 (or FP16
 deviations); the oracle computes in FP64.  A population's error is stated
 relative to its lattice weight times a reference density of 1 (the
-majority phase).  FP32: 1e-5 for short runs (a few hundred steps); for the
-2000-step small capillary 1e-4, twice what the oracle's own formulas give
-when evaluated in FP32 (test_fp32_bound.py: the moving meniscus integrates
-FP32 rounding, about 3e-8 per step).  FP16 storage: a measured bound,
+majority phase).  FP32: 1e-5, also over the 2000 steps of the small
+capillary, where the moving meniscus integrates FP32 rounding: the
+textbook formulas evaluated in FP32 drift to 6e-5 there
+(test_fp32_bound.py); the kernels' pairwise equilibrium and rest-population
+mass closure stay near 6e-6.  FP16 storage: a measured bound,
 stated with its test.  Integer and index results -- the solid mask, the
 step a node turns solid, the pore-closure step -- must match exactly; the
 front position within 0.5 lattice units.
@@ -25,8 +26,7 @@ from tests.gpu_helpers import (elementwise_rel, oracle_for, oracle_pops,
 
 pytestmark = pytest.mark.gpu
 
-FP32_TOL = 1e-5        # up to a few hundred steps
-FP32_TOL_LONG = 1e-4   # 2000 steps of the small capillary
+FP32_TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -94,11 +94,9 @@ def test_small_capillary_2000_steps():
             assert np.isnan(go["front"])
         else:
             assert abs(go["front"] - oo["front"]) < 0.5
-        if o.step_count <= 500:
-            assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+        assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
     err = pop_error(s.populations(), oracle_pops(o))
     print("small capillary: max population error / w_i = %.3g" % err)
-    assert err < FP32_TOL_LONG
     go = s.observables()[0]
     oo = A.lattice_observables(o)
     assert go["closure_step"] == o.closure_step
@@ -155,7 +153,7 @@ def test_paper_scale_capillary_full_size():
     # launch configuration the benchmark times, for a stretch the oracle
     # finishes in seconds, compared element by element.
     geom, mp, _ = I.config_paper_scale(k_r=1e-3)
-    mp.m_threshold = 0.02   # growth inside the short stretch
+    mp.m_threshold = 0.004  # growth inside the short stretch
     s, o = _pair(geom, mp)
     s.step(12)
     o.step(12)
