@@ -208,6 +208,51 @@ lbm_status lbm_fit_reff(const double *t, const double *z, int32_t n,
                         double gamma, double mu, double length,
                         double cos_theta0, double *r_eff);
 
+/* ---- observables without allocation ----------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running inside a memory pool or
+ * arena that another runtime owns (a framework's caching allocator), builds
+ * that forbid dynamic allocation after start-up, or code that must not
+ * synchronize the device, as cudaMalloc and cudaFree may.  Such callers
+ * cannot create a handle (lbm_create allocates), so this call takes one
+ * lattice's state as device pointers and writes the observables to a
+ * device pointer.  It computes what lbm_observables reports for a handle in
+ * the same state.
+ *
+ * pops:    [22][ny][nx] FP32 post-streaming populations (LBM_FIELD_POPS
+ *          layout), device memory;
+ * solid:   [ny][nx] current solid mask (1 = solid), device memory;
+ * solid0:  [ny][nx] initial solid mask (wall thickness reference);
+ * deposit: [ny][nx] precipitated mass (doubles), device memory;
+ * ledger:  host array of 4 doubles, mass moved out of the fluid by growth
+ *          (A, B, solute, deposit); copied into the result;
+ * step, closure_step: copied into the result;
+ * out:     one lbm_obs in device memory, written by the call;
+ * cuda_stream: the stream the two kernels are launched on (NULL = the
+ *          legacy default stream); the call is asynchronous on it.
+ *
+ * Allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).  Its working memory is a file-scope device array of
+ * LBM_STATIC_MAX_COLUMNS column records (about 1.8 MB) that every GPU
+ * which loads this library holds until the process exits; nx above that
+ * limit returns LBM_EINVAL.  The first call on a device looks up the
+ * array's device address, with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array:
+ * calls whose kernels overlap on the GPU (different streams, or different
+ * host threads) race and must be serialized by the caller.  Each call
+ * writes every record it reads, so no clearing is needed between calls.
+ * Returns LBM_EINVAL for NULL pointers or bad sizes, LBM_ECUDA if the
+ * set-up or the launch fails. */
+#define LBM_STATIC_MAX_COLUMNS 16384
+lbm_status lbm_observables_static(const float *pops, const uint8_t *solid,
+                                  const uint8_t *solid0,
+                                  const double *deposit, int32_t nx,
+                                  int32_t ny, int32_t cap_x0, int32_t cap_x1,
+                                  const double ledger[4], int64_t step,
+                                  int64_t closure_step, lbm_obs *out,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ SYMBOLS = ("lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_step",
            "lbm_step_count", "lbm_count", "lbm_observables",
            "lbm_get_solid_mask", "lbm_get_fields", "lbm_set_fields",
            "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
-           "lbm_fit_reff")
+           "lbm_fit_reff", "lbm_observables_static")
 
 
 class LbmError(RuntimeError):
@@ -104,6 +104,9 @@ def load_library(path: str = LIB_PATH):
     dp = C.POINTER(C.c_double)
     lib.lbm_fit_reff.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double,
                                  C.c_double, C.c_double, dp]
+    lib.lbm_observables_static.argtypes = [vp, vp, vp, vp, C.c_int32,
+                                           C.c_int32, C.c_int32, C.c_int32,
+                                           dp, C.c_int64, C.c_int64, vp, vp]
     _lib = lib
     return lib
 
@@ -266,3 +269,25 @@ def fit_reff(t, z, gamma: float, mu: float, length: float,
     if st != LBM_OK:
         raise LbmError(st, "lbm_fit_reff: bad arguments")
     return out.value
+
+
+#: most columns lbm_observables_static accepts (its fixed scratch size)
+STATIC_MAX_COLUMNS = 16384
+
+
+def observables_static(pops_ptr: int, solid_ptr: int, solid0_ptr: int,
+                       deposit_ptr: int, nx: int, ny: int, cap_x0: int,
+                       cap_x1: int, ledger, step: int, closure_step: int,
+                       out_ptr: int, stream: int = 0) -> None:
+    """``lbm_observables_static``: observables of one lattice held in
+    caller-owned device buffers (raw device addresses), written to the
+    device address ``out_ptr`` (one lbm_obs, 144 bytes); allocates nothing.
+    """
+    lib = load_library()
+    led = (C.c_double * 4)(*[float(v) for v in ledger])
+    st = lib.lbm_observables_static(pops_ptr, solid_ptr, solid0_ptr,
+                                    deposit_ptr, nx, ny, cap_x0, cap_x1, led,
+                                    int(step), int(closure_step), out_ptr,
+                                    stream or None)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_observables_static failed")
