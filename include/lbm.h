@@ -193,6 +193,26 @@ lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
 lbm_status lbm_save(lbm_handle *h, const char *path);
 lbm_status lbm_load(lbm_handle *h, const char *path);
 
+/* Step-kernel variant in use: kernel 0 = direct global loads, 1 =
+ * TMA-staged tiles (default); tile of tx by ty nodes per block. */
+typedef struct lbm_tuning {
+    int32_t kernel;
+    int32_t tx, ty;
+    double ms_per_step;  /* measured by lbm_autotune, 0 otherwise */
+} lbm_tuning;
+
+/* Autotuner for the step kernel (project addition; the paper describes no
+ * implementation).  Times every supported variant (direct or TMA-staged,
+ * tile shapes 32x4, 32x8, 32x16, 64x4, 64x8) for `steps` steps on this
+ * handle's own state, restores the state after each trial, and keeps the
+ * fastest; every variant computes bit-identical results, so only speed
+ * differs.  Synchronizes; allocates a temporary copy of the state for the
+ * trials.  out (may be NULL) receives the choice.  steps >= 1. */
+lbm_status lbm_autotune(lbm_handle *h, int32_t steps, lbm_tuning *out);
+
+/* The variant in use. */
+lbm_status lbm_get_tuning(const lbm_handle *h, lbm_tuning *out);
+
 /* Frees everything; NULL is allowed. */
 void lbm_destroy(lbm_handle *h);
 

@@ -56,7 +56,7 @@ static_assert(sizeof(lbm_obs) == 8 * 16 + 4 * 2 + 8, "lbm_obs layout");
 struct lbm_handle {
     int count = 0;
     bool half = false;
-    int tx = 32, ty = 8;
+    int tx = 32, ty = 16;  // tile of the step kernel (LBM_TILE overrides)
     bool use_tma = true;
     std::vector<LatDesc> desc;
     std::vector<int64_t> col_base;   // first column of lattice l (all columns)
@@ -89,6 +89,8 @@ struct lbm_handle {
     CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
     int *d_sched = nullptr;            // TMA kernel: tiles of each block
     int sched_grid = 0, sched_slots = 0;
+    cudaGraphExec_t graph = nullptr;   // kGraphSteps steps from cur == 0
+    bool use_graph = true;
     int *d_err = nullptr;              // kernel error flags
     int cur = 0;
     int64_t steps = 0;
@@ -131,6 +133,7 @@ static void free_all(lbm_handle *h) {
                   h->d_sched};
     for (void *p : ps)
         if (p) cudaFree(p);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own) cudaStreamDestroy(h->own);
 }
 
@@ -167,6 +170,8 @@ static void pick_tile(lbm_handle *h) {
     }
     const char *k = getenv("LBM_KERNEL");
     if (k && strcmp(k, "direct") == 0) h->use_tma = false;
+    const char *gr = getenv("LBM_GRAPH");
+    if (gr && strcmp(gr, "0") == 0) h->use_graph = false;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -197,12 +202,13 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     for (int b = 0; b < 2; ++b) {
         for (int l = 0; l < count; ++l) {
             const LatDesc &d = h->desc[l];
-            cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NPOP};
+            const cuuint64_t rows = (cuuint64_t)(d.ny + 2 * GHOST);
+            cuuint64_t dims[3] = {(cuuint64_t)d.nx, rows, (cuuint64_t)NPOP};
             cuuint64_t strides[2] = {(cuuint64_t)d.pitch * esz, (cuuint64_t)d.plane * esz};
             cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx, h->half),
                                  (cuuint32_t)(h->ty + 4), (cuuint32_t)NPOP};
             cuuint32_t es[3] = {1, 1, 1};
-            void *base = (char *)h->d_pop[b] + (size_t)d.pop_off * esz;
+            void *base = (char *)h->d_pop[b] + (size_t)(d.pop_off - GHOST * d.pitch) * esz;
             CUresult r = enc(&maps[b * count + l],
                              h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -217,9 +223,9 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                 return false;
             }
             if (h->half) {
-                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NMOM};
+                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, rows, (cuuint64_t)NMOM};
                 cuuint32_t mbox[3] = {box[0], box[1], (cuuint32_t)NMOM};
-                void *mbase = (char *)h->d_mom[b] + (size_t)d.mom_off * 2;
+                void *mbase = (char *)h->d_mom[b] + (size_t)(d.mom_off - GHOST * d.pitch) * 2;
                 r = enc(&moms[b * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                         mbase, mdims, strides, mbox, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -236,12 +242,12 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     std::vector<CUtensorMap> mmaps(count);
     for (int l = 0; l < count; ++l) {
         const LatDesc &d = h->desc[l];
-        cuuint64_t dims[2] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny};
+        cuuint64_t dims[2] = {(cuuint64_t)d.nx, (cuuint64_t)(d.ny + 2 * GHOST)};
         cuuint64_t strides[1] = {(cuuint64_t)d.pitch};
         cuuint32_t box[2] = {(cuuint32_t)tma_mask_box_x(h->tx), (cuuint32_t)(h->ty + 4)};
         cuuint32_t es[2] = {1, 1};
         CUresult r = enc(&mmaps[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                         h->d_mask + d.node_off, dims, strides, box, es,
+                         h->d_mask + d.node_off - GHOST * d.pitch, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -325,6 +331,52 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
     return true;
 }
 
+// Re-tiles every lattice for another step kernel or tile shape: tile
+// counts in the descriptors, the tile -> lattice table and, for the TMA
+// kernel, the tensor maps and the block schedule.  Drops the captured graph.
+static lbm_status retile(lbm_handle *h, bool tma, int tx, int ty) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->use_tma = tma;
+    h->tx = tx;
+    h->ty = ty;
+    int tiles = 0;
+    for (auto &d : h->desc) {
+        d.tiles_x = (d.nx + tx - 1) / tx;
+        d.tile_base = tiles;
+        tiles += d.tiles_x * ((d.ny + ty - 1) / ty);
+    }
+    std::vector<int32_t> tile_lat(tiles);
+    for (int l = 0; l < h->count; ++l) {
+        const LatDesc &d = h->desc[l];
+        const int nt = d.tiles_x * ((d.ny + ty - 1) / ty);
+        for (int k = 0; k < nt; ++k) tile_lat[d.tile_base + k] = l;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->d_tile_lat) cudaFree(h->d_tile_lat);
+    h->d_tile_lat = nullptr;
+    CK(h, dalloc(&h->d_tile_lat, tiles));
+    CK(h, cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t),
+                     cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->d_desc, h->desc.data(), h->count * sizeof(LatDesc),
+                     cudaMemcpyHostToDevice));
+    h->ntiles = tiles;
+    for (CUtensorMap **m : {&h->d_maps, &h->d_mom_maps, &h->d_mask_maps}) {
+        if (*m) cudaFree(*m);
+        *m = nullptr;
+    }
+    if (h->d_sched) cudaFree(h->d_sched);
+    h->d_sched = nullptr;
+    if (tma) {
+        std::string why;
+        if (!make_maps(h, why) || !make_schedule(h, why))
+            return fail(h, LBM_EINVAL, "tile shape not supported: " + why);
+    }
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
                                        const lbm_params *p, int32_t count,
                                        lbm_handle **out) {
@@ -341,7 +393,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
                         "lattice " + std::to_string(l) +
                             ": need nx >= 1, ny >= 3 and all arrays");
         // 32-bit offsets inside a lattice: 22 planes of ny * pitch elements
-        if ((int64_t)NPOP * G.ny * ((G.nx + 31) / 32 * 32) >= ((int64_t)1 << 31))
+        if ((int64_t)NPOP * (G.ny + 2 * GHOST) * ((G.nx + 31) / 32 * 32) >= ((int64_t)1 << 31))
             return fail(nullptr, LBM_EINVAL, "lattice too large");
         if (!(0 <= G.cap_x0 && G.cap_x0 < G.cap_x1 && G.cap_x1 <= G.nx))
             return fail(nullptr, LBM_EINVAL,
@@ -376,10 +428,11 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.cap_x0 = G.cap_x0;
         d.cap_x1 = G.cap_x1;
         d.inlet = P.inlet ? 1 : 0;
-        d.plane = (int64_t)d.ny * d.pitch;
-        d.node_off = node;
-        d.pop_off = pop;
-        d.mom_off = mom;
+        // planes include GHOST rows on both sides; offsets point at row 0
+        d.plane = (int64_t)(d.ny + 2 * GHOST) * d.pitch;
+        d.node_off = node + GHOST * d.pitch;
+        d.pop_off = pop + GHOST * d.pitch;
+        d.mom_off = mom + GHOST * d.pitch;
         d.col_off = sec;
         node += d.plane;
         pop += NPOP * d.plane;
@@ -419,10 +472,12 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         for (int k = 0; k < nt; ++k) tile_lat[d.tile_base + k] = l;
         for (int x = 0; x < d.nx; ++x) col_lat[h->col_base[l] + x] = l;
         const uint8_t *S = g[l].solid;
-        for (int y = 0; y < d.ny; ++y)
+        for (int y = -GHOST; y < d.ny + GHOST; ++y) {
+            const int ys = (y + d.ny) % d.ny;  // row y or its periodic image
             for (int x = 0; x < d.nx; ++x)
                 mask[d.node_off + (int64_t)y * d.pitch + x] =
-                    S[(int64_t)y * d.nx + x] ? 7 : 0;
+                    S[(int64_t)ys * d.nx + x] ? 7 : 0;
+        }
         for (int x = d.cap_x0; x < d.cap_x1; ++x) {
             int fl = 0, b = 0, t = 0;
             for (int y = 0; y < d.ny; ++y) fl += S[(int64_t)y * d.nx + x] == 0;
@@ -587,9 +642,62 @@ static StepArgs step_args(lbm_handle *h) {
     return a;
 }
 
+static cudaError_t launch_one(lbm_handle *h) {
+    StepArgs a = step_args(h);
+    return h->use_tma
+               ? launch_step_tma(a, h->d_maps + h->cur * h->count,
+                                 h->half ? h->d_mom_maps + h->cur * h->count : nullptr,
+                                 h->d_mask_maps, h->d_sched, h->sched_slots,
+                                 h->sched_grid, h->tx, h->ty, h->half, h->d_err,
+                                 h->stream)
+               : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
+}
+
+// Steps per captured graph: even, so a replay starts and ends with the
+// same population buffer as input.
+static const int kGraphSteps = 16;
+
+// Captures kGraphSteps launches starting from buffer 0 into h->graph.
+static lbm_status capture_graph(lbm_handle *h) {
+    const int cur0 = h->cur;
+    h->cur = 0;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        e = launch_one(h);
+        h->cur ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    h->cur = cur0;
+    CK(h, e);
+    CK(h, e2);
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e3);
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
     if (!h || n < 0) return fail(h, LBM_EINVAL, "bad handle or n < 0");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    // whole groups of kGraphSteps steps replay one captured graph (the
+    // step count lives on the device, so the graph needs no new arguments)
+    while (h->use_graph && n >= kGraphSteps + (h->cur ? 1 : 0)) {
+        if (h->cur) {  // one plain step to get back to buffer 0
+            CK(h, launch_one(h));
+            h->cur ^= 1;
+            h->steps += 1;
+            n -= 1;
+        }
+        if (!h->graph) {
+            lbm_status st = capture_graph(h);
+            if (st != LBM_OK) return st;
+        }
+        CK(h, cudaGraphLaunch(h->graph, h->stream));
+        h->steps += kGraphSteps;
+        n -= kGraphSteps;
+    }
     for (int64_t k = 0; k < n; ++k) {
         StepArgs a = step_args(h);
         cudaError_t e =
@@ -641,8 +749,9 @@ extern "C" lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k,
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     const LatDesc &d = h->desc[k];
     if (n != (size_t)d.nx * d.ny) return fail(h, LBM_EINVAL, "size mismatch");
-    std::vector<uint8_t> raw(d.plane);
-    CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, d.plane,
+    const size_t rows_bytes = (size_t)d.ny * d.pitch;
+    std::vector<uint8_t> raw(rows_bytes);
+    CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, rows_bytes,
                           cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     const MaskBits mb(h->steps);
@@ -714,17 +823,18 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
         if (bytes != N * 8) return fail(h, LBM_EINVAL, "size mismatch");
         lbm_status s = settle(h, k);
         if (s != LBM_OK) return s;
-        std::vector<uint8_t> raw(d.plane);
-        CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, d.plane,
+        const size_t rows_n = (size_t)d.ny * d.pitch;
+        std::vector<uint8_t> raw(rows_n);
+        CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, rows_n,
                               cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
-        std::vector<double> m(d.plane, 0.0);
+        std::vector<double> m(rows_n, 0.0);
         const double *src = static_cast<const double *>(host);
         for (int y = 0; y < d.ny; ++y)
             for (int x = 0; x < d.nx; ++x)
                 if (!(raw[(size_t)y * d.pitch + x] & 7))
                     m[(size_t)y * d.pitch + x] = src[(size_t)y * d.nx + x];
-        CK(h, cudaMemcpyAsync(h->d_m + d.node_off, m.data(), d.plane * 8,
+        CK(h, cudaMemcpyAsync(h->d_m + d.node_off, m.data(), rows_n * 8,
                               cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
         return LBM_OK;
@@ -854,5 +964,106 @@ extern "C" lbm_status lbm_fit_reff(const double *t, const double *z,
     if (!(den > 0)) return LBM_EINVAL;
     const double v = num / den;
     *r_eff = 3.0 * mu * length * v / (gamma * cos_theta0);
+    return LBM_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------
+
+extern "C" lbm_status lbm_get_tuning(const lbm_handle *h, lbm_tuning *out) {
+    if (!h || !out) return LBM_EINVAL;
+    out->kernel = h->use_tma ? 1 : 0;
+    out->tx = h->tx;
+    out->ty = h->ty;
+    out->ms_per_step = 0.0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_autotune(lbm_handle *h, int32_t steps,
+                                   lbm_tuning *out) {
+    if (!h || steps < 1) return fail(h, LBM_EINVAL, "bad handle or steps < 1");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    CK(h, cudaStreamSynchronize(h->stream));
+    // snapshot of everything a step changes
+    const size_t esz = h->half ? 2 : 4;
+    struct Piece { void *dev; size_t bytes; };
+    const int cur0 = h->cur;
+    const int64_t steps0 = h->steps;
+    std::vector<Piece> parts = {
+        {h->d_pop[cur0], (size_t)h->pop_elems * esz},
+        {h->d_mask, (size_t)h->node_elems},
+        {h->d_m, (size_t)h->node_elems * 8},
+        {h->d_col_fluid, (size_t)h->nsec * 4},
+        {h->d_st, (size_t)h->count * sizeof(LatState)},
+        {h->d_step, 8}};
+    if (h->half) parts.push_back({h->d_mom[cur0], (size_t)h->mom_elems * 2});
+    size_t total = 0;
+    for (auto &p : parts) total += (p.bytes + 255) / 256 * 256;
+    char *snap = nullptr;
+    if (cudaMalloc(&snap, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LBM_ENOMEM, "autotune: no room for a state copy");
+    }
+    auto copy_all = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (auto &p : parts) {
+            cudaError_t e = save ? cudaMemcpyAsync(snap + off, p.dev, p.bytes,
+                                                   cudaMemcpyDeviceToDevice, h->stream)
+                                 : cudaMemcpyAsync(p.dev, snap + off, p.bytes,
+                                                   cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return e;
+            off += (p.bytes + 255) / 256 * 256;
+        }
+        return cudaStreamSynchronize(h->stream);
+    };
+    struct Cand { bool tma; int tx, ty; };
+    const Cand cands[] = {{true, 32, 16}, {true, 32, 8}, {true, 64, 4},
+                          {true, 64, 8},  {true, 32, 4}, {false, 32, 8},
+                          {false, 32, 4}, {false, 64, 4}};
+    const Cand orig = {h->use_tma, h->tx, h->ty};
+    Cand best = orig;
+    double best_ms = 1e300;
+    lbm_status st = LBM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = copy_all(true);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    for (const Cand &c : cands) {
+        if (ce != cudaSuccess || st != LBM_OK) break;
+        if (retile(h, c.tma, c.tx, c.ty) != LBM_OK) {
+            st = LBM_OK;  // shape not available on this device: skip it
+            h->err.clear();
+            continue;
+        }
+        st = lbm_step(h, kGraphSteps + 2);  // warm-up, graph capture
+        if (st != LBM_OK) break;
+        const int n = (steps + kGraphSteps - 1) / kGraphSteps * kGraphSteps;
+        ce = cudaEventRecord(e0, h->stream);
+        if (ce == cudaSuccess) st = lbm_step(h, n);
+        if (ce == cudaSuccess && st == LBM_OK) ce = cudaEventRecord(e1, h->stream);
+        if (ce == cudaSuccess && st == LBM_OK) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess && st == LBM_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce == cudaSuccess && st == LBM_OK && ms / n < best_ms) {
+            best_ms = ms / n;
+            best = c;
+        }
+        // back to the saved state
+        if (ce == cudaSuccess) ce = copy_all(false);
+        h->cur = cur0;
+        h->steps = steps0;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (st != LBM_OK) return st;
+    CK(h, ce);
+    lbm_status r = retile(h, best.tma, best.tx, best.ty);
+    if (r != LBM_OK) return r;
+    if (out) {
+        out->kernel = best.tma ? 1 : 0;
+        out->tx = best.tx;
+        out->ty = best.ty;
+        out->ms_per_step = best_ms;
+    }
     return LBM_OK;
 }

@@ -19,7 +19,8 @@ __device__ __forceinline__ float load_pop(const void *base, const __half *mom,
     const float dv = __half2float(static_cast<const __half *>(base)[d.pop_off + q * d.plane + e]);
     const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
     const float rt = __half2float(mom[d.mom_off + comp * d.plane + e]);
-    return comp < 2 ? wq(q - comp * Q) * (rt + dv) : 0.25f * (rt + dv);
+    return comp < 2 ? __fmul_rn(wq(q - comp * Q), __fadd_rn(rt, dv))
+                    : __fmul_rn(0.25f, __fadd_rn(rt, dv));
 }
 
 // Post-streaming populations of node (x, y) at the current step: 22 values
@@ -124,6 +125,8 @@ __global__ void k_unstream(const LatDesc *desc, int l, const float *canon,
         v[2 * Q + k] = canon[(2 * Q + (b ? sopp(k) : k)) * P + src];
     }
     store_node(fout, mout, d, half, own, v);
+    if (y < GHOST) store_node(fout, mout, d, half, own + (int64_t)d.ny * d.pitch, v);
+    if (y >= d.ny - GHOST) store_node(fout, mout, d, half, own - (int64_t)d.ny * d.pitch, v);
 }
 
 // Post-streaming fields of lattice l at step t into canon ([22][ny][nx]);
@@ -199,7 +202,7 @@ __global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
     const MaskBits mb(t);
     uint8_t *mask = mask_all + d.node_off;
     const int64_t own = (int64_t)y * d.pitch + x;
-    mask[own] = (mask[own] & mb.force) ? 7 : 0;
+    mask_store(mask, (int)own, y, d.ny, d.pitch, (mask[own] & mb.force) ? 7 : 0);
 }
 
 // ---------------------------------------------------------------------------

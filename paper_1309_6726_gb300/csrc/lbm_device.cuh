@@ -8,6 +8,12 @@
 //     starts on a 128-byte boundary in FP32 storage);
 //   FP16 storage adds 3 moment planes per lattice and buffer (rho_A,
 //     rho_B, C rounded to FP16) that the deviations are taken from;
+//   every plane (populations, moments, mask) has two ghost rows above and
+//     below the lattice, rows -2, -1 and ny, ny + 1, holding copies of rows
+//     ny - 2, ny - 1 and 0, 1 (the periodic images): the offsets below point
+//     at row 0, so row y of a plane is at offset y * pitch for -2 <= y <
+//     ny + 2, and the nodes next to the y boundaries refresh the copies
+//     whenever they write;
 //   mask: one byte per node, read and written in place (see MaskBits);
 //   deposit: one double per node;
 //   per section column: fluid-node counter (closure), initial wall
@@ -74,7 +80,7 @@ struct alignas(16) LatDesc {
     int64_t node_off;   // first node of this lattice in mask / deposit
     int64_t pop_off;    // first element of plane 0 in a population buffer
     int64_t mom_off;    // first element of moment plane 0 (FP16 storage)
-    int64_t plane;      // ny * pitch
+    int64_t plane;      // (ny + 4) * pitch: rows -2 .. ny + 1
     int64_t col_off;    // first section column in per-column arrays
     float tau_a, tau_b, inv_tau_a, inv_tau_b, inv_tau_d;
     float g_coh, g_ads, k_r, c_in, body_x;
@@ -116,6 +122,26 @@ struct StepArgs {
     int64_t *step;          // completed steps (read at start, bumped at end)
     unsigned int *done;     // blocks finished in this launch
 };
+
+constexpr int GHOST = 2;  // ghost rows on each side in y
+
+// Offsets of the ghost copies of row y (0 or 1, or ny - 2 or ny - 1):
+// returns how many (0, 1 or 2; 2 only when ny < 4) and writes them to g[].
+__device__ __forceinline__ int ghost_rows(int y, int ny, int pitch, int own,
+                                          int g[2]) {
+    int n = 0;
+    if (y < GHOST) g[n++] = own + ny * pitch;
+    if (y >= ny - GHOST) g[n++] = own - ny * pitch;
+    return n;
+}
+
+// Stores a mask byte of row y and its ghost copies.
+__device__ __forceinline__ void mask_store(uint8_t *mask, int own, int y,
+                                           int ny, int pitch, uint8_t v) {
+    mask[own] = v;
+    if (y < GHOST) mask[own + ny * pitch] = v;
+    if (y >= ny - GHOST) mask[own - ny * pitch] = v;
+}
 
 // Periodic index for any offset (lattices smaller than a tile included).
 __device__ __forceinline__ int wrapg(int a, int n) {

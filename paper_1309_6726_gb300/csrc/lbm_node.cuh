@@ -122,6 +122,22 @@ __device__ __forceinline__ void store4(typename S::T *__restrict__ p,
     }
 }
 
+// Writes the 22 post-collision values of a node at plane offset `off`.
+template <class S>
+__device__ __forceinline__ void store_node22(const StepArgs &a,
+                                             const LatDesc &d, int off,
+                                             const float fA[Q],
+                                             const float fB[Q],
+                                             const float g[QS]) {
+    using T = typename S::T;
+    const int pl = (int)d.plane;
+    T *p = static_cast<T *>(a.fout) + d.pop_off + off;
+    __half *mp = S::kHalf ? a.mout + d.mom_off + off : nullptr;
+    store9<S>(p, mp, pl, fA);
+    store9<S>(p + Q * pl, S::kHalf ? mp + pl : nullptr, pl, fB);
+    store4<S>(p + 2 * Q * pl, S::kHalf ? mp + 2 * pl : nullptr, pl, g);
+}
+
 // Everything after the pull, for a node that is fluid in s_t.
 //   fA, fB, g: post-streaming populations of the node (g pulled already);
 //   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
@@ -129,7 +145,7 @@ __device__ __forceinline__ void store4(typename S::T *__restrict__ p,
 // Returns true if the node reached the threshold in this step.
 template <class S>
 __device__ __forceinline__ bool fluid_update(
-    const StepArgs &a, const LatDesc &d, int l, long long t, int gx,
+    const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
     int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
     const float rhoB_nb[Q], unsigned snb, int ns) {
     using T = typename S::T;
@@ -198,12 +214,10 @@ __device__ __forceinline__ bool fluid_update(
         }
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
-    T *p = static_cast<T *>(a.fout) + d.pop_off + own;
-    const int pl = (int)d.plane;
-    __half *mp = S::kHalf ? a.mout + d.mom_off + own : nullptr;
-    store9<S>(p, mp, pl, fA);
-    store9<S>(p + Q * pl, S::kHalf ? mp + pl : nullptr, pl, fB);
-    store4<S>(p + 2 * Q * pl, S::kHalf ? mp + 2 * pl : nullptr, pl, g);
+    store_node22<S>(a, d, own, fA, fB, g);
+    // ghost copies of rows next to the y boundaries
+    if (gy < GHOST) store_node22<S>(a, d, own + d.ny * d.pitch, fA, fB, g);
+    if (gy >= d.ny - GHOST) store_node22<S>(a, d, own - d.ny * d.pitch, fA, fB, g);
     return flagged;
 }
 

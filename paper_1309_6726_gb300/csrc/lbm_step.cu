@@ -67,7 +67,7 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
-            f[i] = wq(i) * (rt + dv);
+            f[i] = __fmul_rn(wq(i), __fadd_rn(rt, dv));  // no fusing (see TMA kernel)
         }
     }
 }
@@ -93,7 +93,7 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
-            g[k] = 0.25f * (ct + dv);
+            g[k] = __fmul_rn(0.25f, __fadd_rn(ct, dv));
         }
     }
 }
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TX *TY)
                 pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
                 retire_node(a, d, l, own, fA, fB, g);
             }
-            if (nb != s_own) mask[own] = nb;
+            if (nb != s_own) mask_store(mask, own, gy, ny, d.pitch, nb);
         } else {
             float g[QS], rAn[Q], rBn[Q];
             unsigned snb = 0;
@@ -205,9 +205,9 @@ __global__ void __launch_bounds__(TX *TY)
                 if (smask[hy + cy(i)][hx + cx(i)] & mb.force) snb |= 1u << i;
             }
             pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
-            const bool flagged = fluid_update<S>(a, d, l, t, gx, own, fA, fB, g,
+            const bool flagged = fluid_update<S>(a, d, l, t, gx, gy, own, fA, fB, g,
                                                  rAn, rBn, snb, ns);
-            if (flagged) mask[own] = s_own | mb.next;
+            if (flagged) mask_store(mask, own, gy, ny, d.pitch, s_own | mb.next);
         }
     }
     finish_launch(a, t);

@@ -153,8 +153,11 @@ __device__ __forceinline__ void spull9(const typename S::T *tile,
         if constexpr (!S::kHalf) {
             f[i] = tile[q * TT::PL + cell];
         } else {
-            f[i] = wq(i) * (__half2float(mom[comp * TT::PL + cell]) +
-                            __half2float(tile[q * TT::PL + cell]));
+            // explicit roundings: no fused multiply-add may merge this
+            // product into a later sum, so every pull of a node's
+            // population (own node or density ring) gives the same bits
+            f[i] = __fmul_rn(wq(i), __fadd_rn(__half2float(mom[comp * TT::PL + cell]),
+                                              __half2float(tile[q * TT::PL + cell])));
         }
     }
 }
@@ -171,8 +174,8 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
         if constexpr (!S::kHalf) {
             g[k] = tile[q * TT::PL + cell];
         } else {
-            g[k] = 0.25f * (__half2float(mom[2 * TT::PL + cell]) +
-                            __half2float(tile[q * TT::PL + cell]));
+            g[k] = __fmul_rn(0.25f, __fadd_rn(__half2float(mom[2 * TT::PL + cell]),
+                                              __half2float(tile[q * TT::PL + cell])));
         }
     }
 }
@@ -234,8 +237,7 @@ __global__ void __launch_bounds__(TX *TY)
         const int local = tile - gd->tile_base;
         const int tiles_x = gd->tiles_x;
         const int x0 = (local % tiles_x) * TX;
-        const int y0 = (local / tiles_x) * TY - 2;
-        s_tile[slot] = tile;
+        const int y0 = (local / tiles_x) * TY;  // row ty0 - 2 of the plane
         fence_proxy_async();
         mbar_expect_tx(&bar[s], TT::TX_BYTES);
         bulk_load(sdesc(slot), gd, 128, &bar[s]);
@@ -250,16 +252,18 @@ __global__ void __launch_bounds__(TX *TY)
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         *s_t = *(volatile long long *)a.step;
-        const int t0 = sched_at(0), t1 = sched_at(1);
+        const int t0 = sched_at(0), t1 = t0 >= 0 ? sched_at(1) : -1;
+        s_tile[0] = t0;
+        s_tile[1] = t1;
         if (t0 >= 0) issue(t0, 0, 0);
-        if (t0 >= 0 && t1 >= 0) issue(t1, 1, 1);
+        if (t1 >= 0) issue(t1, 1, 1);
     }
     __syncthreads();
     const long long t = *s_t;
     const MaskBits mb(t);
 
     unsigned parity = 0u;  // bit s: phase parity of stage s
-    for (int k = 0; sched_at(k) >= 0; ++k) {
+    for (int k = 0; s_tile[k % 3] >= 0; ++k) {
         const int s = k & 1;
         const int slot = k % 3;
         const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(TX *TY)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(err, 1);
-                if (sched_at(k + 1) >= 0)
+                if (s_tile[(k + 1) % 3] >= 0)
                     mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
             }
             break;
@@ -279,13 +283,14 @@ __global__ void __launch_bounds__(TX *TY)
         const int local = tile - d.tile_base;
         const int tx0 = (local % d.tiles_x) * TX;
         const int ty0 = (local / d.tiles_x) * TY;
-        const bool edge = tx0 < 2 || ty0 < 2 || tx0 + TX + 2 > nx ||
-                          ty0 + TY + 2 > ny;
+        // rows come from the ghost rows near the y boundaries; only tiles
+        // at the x ends need the periodic images of halo columns
+        const bool edge = tx0 < 2 || tx0 + TX + 2 > nx;
         T *tp = stage_pop(s);
         __half *tm = stage_mom(s);
         uint8_t *sm = stage_mask(s);
 
-        // periodic images of halo cells outside the lattice (the copies
+        // periodic images of halo columns outside the lattice (the copies
         // filled them with zeros); one thread per such cell, all planes;
         // cells spread over the warps
         // rows / columns of the tile that hold lattice nodes; the frame
@@ -301,9 +306,9 @@ __global__ void __launch_bounds__(TX *TY)
                 if (e >= RH * CW) continue;
                 const int yy = e / CW;
                 const int xc = e - yy * CW - 2;  // column relative to x0
-                const int gy = ty0 - 2 + yy, gx = tx0 + xc;
-                if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-                const int g = wrapg(gy, ny) * d.pitch + wrapg(gx, nx);
+                const int gy = ty0 - 2 + yy, gx = tx0 + xc;  // gy: -2 .. ny + 1
+                if (gx >= 0 && gx < nx) continue;
+                const int g = gy * d.pitch + wrapg(gx, nx);
                 const int cell = yy * TT::BX + xc + TT::XO;
 #pragma unroll 2
                 for (int q = 0; q < NPOP; ++q)
@@ -374,7 +379,8 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         // stage s is free: start the copy of the tile after next into it
         if (tid == 0) {
-            const int t2 = sched_at(k + 2);
+            const int t2 = s_tile[(k + 1) % 3] >= 0 ? sched_at(k + 2) : -1;
+            s_tile[(k + 2) % 3] = t2;
             if (t2 >= 0) issue(t2, s, (k + 2) % 3);
         }
 
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(TX *TY)
             if (s_own & mb.force) {
                 if (own_pull_fluid) retire_node(a, d, l, own, fA, fB, g);
                 const uint8_t nb = s_own | mb.next;
-                if (nb != s_own) a.mask[d.node_off + own] = nb;
+                if (nb != s_own) mask_store(a.mask + d.node_off, own, y, ny, d.pitch, nb);
             } else {
                 float rAn[Q], rBn[Q];
 #pragma unroll
@@ -393,9 +399,10 @@ __global__ void __launch_bounds__(TX *TY)
                     rBn[i] = fr[TT::RX * TT::RY + fc];
                 }
                 const int ns = __popc(snb & 0x1Eu);
-                const bool flagged = fluid_update<S>(a, d, l, t, x, own, fA, fB, g,
+                const bool flagged = fluid_update<S>(a, d, l, t, x, y, own, fA, fB, g,
                                                      rAn, rBn, snb, ns);
-                if (flagged) a.mask[d.node_off + own] = s_own | mb.next;
+                if (flagged)
+                    mask_store(a.mask + d.node_off, own, y, ny, d.pitch, s_own | mb.next);
             }
         }
     }

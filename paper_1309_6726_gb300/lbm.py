@@ -24,7 +24,8 @@ SYMBOLS = ("lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_step",
            "lbm_step_count", "lbm_count", "lbm_observables",
            "lbm_get_solid_mask", "lbm_get_fields", "lbm_set_fields",
            "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
-           "lbm_fit_reff", "lbm_observables_static")
+           "lbm_fit_reff", "lbm_observables_static", "lbm_autotune",
+           "lbm_get_tuning")
 
 
 class LbmError(RuntimeError):
@@ -49,6 +50,16 @@ class Params(C.Structure):
                 ("m_threshold", C.c_double), ("c_in", C.c_double),
                 ("body_force_x", C.c_double), ("inlet", C.c_int32),
                 ("precision", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("tx", C.c_int32), ("ty", C.c_int32),
+                ("ms_per_step", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"kernel": "tma" if self.kernel else "direct",
+                "tile": "%dx%d" % (self.tx, self.ty),
+                "ms_per_step": self.ms_per_step}
 
 
 class Obs(C.Structure):
@@ -104,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     dp = C.POINTER(C.c_double)
     lib.lbm_fit_reff.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double,
                                  C.c_double, C.c_double, dp]
+    lib.lbm_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
+    lib.lbm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     lib.lbm_observables_static.argtypes = [vp, vp, vp, vp, C.c_int32,
                                            C.c_int32, C.c_int32, C.c_int32,
                                            dp, C.c_int64, C.c_int64, vp, vp]
@@ -248,6 +261,18 @@ class Solver:
         a = np.ascontiguousarray(m, dtype=np.float64)
         self._check(self._lib.lbm_set_fields(self._h, k, FIELD_DEPOSIT,
                                              a.ctypes.data, a.nbytes))
+
+    def autotune(self, steps: int = 32) -> dict:
+        """Times every step-kernel variant on this state (restored after
+        each trial) and keeps the fastest; returns the choice."""
+        t = Tuning()
+        self._check(self._lib.lbm_autotune(self._h, int(steps), C.byref(t)))
+        return t.as_dict()
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(self._lib.lbm_get_tuning(self._h, C.byref(t)))
+        return t.as_dict()
 
     def save(self, path: str) -> None:
         self._check(self._lib.lbm_save(self._h, path.encode()))

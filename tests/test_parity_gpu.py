@@ -180,3 +180,105 @@ def test_observables_match_oracle_definitions():
     else:
         assert abs(go["front"] - oo["front"]) < 0.5
     assert go["closure_step"] == o.closure_step
+
+
+# ---- FP16 storage -------------------------------------------------------
+#
+# Populations stored as FP16 deviations from w_i times the node's own
+# FP16-rounded density, FP32 arithmetic.  Stated bounds (measured on the
+# small capillary: 1.1e-3 of w_i after 2000 steps, front within 2e-3 lu,
+# mask and closure step exact; random non-equilibrium states, whose
+# deviations from w_i rho are up to ~0.5 rho: 1.9e-3 after 4 steps):
+FP16_TOL_LONG = 3e-3
+FP16_TOL_SHORT = 5e-3
+
+
+@pytest.mark.parametrize("nx,ny,seed", [(37, 23, 1), (130, 11, 5)])
+def test_fp16_random_state_steps(nx, ny, seed):
+    geom = I.random_lattice(nx, ny, seed=seed, solid_fraction=0.15)
+    mp = I.ModelParams(g_ads=0.4, k_r=0.05, m_threshold=1.0)
+    s, o = _pair(geom, mp, "fp16")
+    f, g = I.random_populations(geom, seed=seed + 100)
+    pops = np.concatenate([f.reshape(18, ny, nx), g])
+    m0 = np.where(geom.solid == 0, 0.995, 0.0)
+    s.set_populations(pops)
+    s.set_deposit(m0)
+    # the FP16 copy of the state is what both sides start from
+    start = s.populations().astype(np.float64)
+    o.set_populations(start[:18].reshape(2, 9, ny, nx))
+    o.set_solute(start[18:])
+    o.set_deposit(m0)
+    assert np.abs(start - pops).max() < 1e-3  # storage rounding itself
+    for n in (1, 3):
+        s.step(n)
+        o.step(n)
+        np.testing.assert_array_equal(s.solid_mask(), o.solid())
+        assert pop_error(s.populations(), oracle_pops(o)) < FP16_TOL_SHORT
+
+
+def test_fp16_small_capillary_2000_steps():
+    geom, mp, steps = I.config_small()
+    s, o = _pair(geom, mp, "fp16")
+    for k in range(steps // 500):
+        s.step(500)
+        o.step(500)
+        go = s.observables()[0]
+        oo = A.lattice_observables(o)
+        np.testing.assert_array_equal(s.solid_mask(), o.solid())
+        if np.isnan(oo["front"]):
+            assert np.isnan(go["front"])
+        else:
+            assert abs(go["front"] - oo["front"]) < 0.5
+    err = pop_error(s.populations(), oracle_pops(o))
+    print("FP16 small capillary: max population error / w_i = %.3g" % err)
+    assert err < FP16_TOL_LONG
+    go = s.observables()[0]
+    oo = A.lattice_observables(o)
+    assert go["closure_step"] == o.closure_step
+    # mass of A (fluid + ledger) drifts only by FP16 rounding of deviations
+    ma = go["mass_a"] + go["ledger_a"]
+    assert ma == pytest.approx(oo["mass_a"] + oo["ledger_a"], rel=1e-4)
+    for key in ("r_min", "r_ave", "r_h", "delta_e", "closed"):
+        assert go[key] == pytest.approx(oo[key], abs=1e-9), key
+
+
+# ---- step-kernel variants, graphs, autotuner ----------------------------
+
+def _batch3():
+    members = [I.SweepMember(14, 90, 2e-2, 30.0, 1.0),
+               I.SweepMember(9, 61, 5e-3, 50.0, 1.3),
+               I.SweepMember(37, 150, 1e-2, 20.0, 0.8)]
+    geoms, mps = zip(*[I.sweep_lattice(m, x_res=16, x_out=8)
+                       for m in members])
+    mps = [I.ModelParams(**{**p.as_dict(), "m_threshold": 0.05}) for p in mps]
+    return list(geoms), mps
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_variants_graphs_and_autotune_bit_identical(monkeypatch, precision):
+    # Every step-kernel variant (direct loads or TMA tiles, any tile shape),
+    # stepping through captured graphs or plain launches, and the autotuned
+    # choice compute the same bits.
+    geoms, mps = _batch3()
+    runs = {}
+    for name, env in (("tma", {}), ("direct", {"LBM_KERNEL": "direct"}),
+                      ("tma64x4", {"LBM_TILE": "64x4"}),
+                      ("nograph", {"LBM_GRAPH": "0"})):
+        for k in ("LBM_KERNEL", "LBM_TILE", "LBM_GRAPH"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        s = lbm.Solver(geoms, mps, precision)
+        s.step(83)
+        runs[name] = [s.populations(k) for k in range(3)]
+        s.close()
+    for k in ("LBM_KERNEL", "LBM_TILE", "LBM_GRAPH"):
+        monkeypatch.delenv(k, raising=False)
+    t = lbm.Solver(geoms, mps, precision)
+    choice = t.autotune(steps=16)
+    assert choice["ms_per_step"] > 0 and t.step_count == 0
+    t.step(83)
+    runs["tuned"] = [t.populations(k) for k in range(3)]
+    for name, pops in runs.items():
+        for k in range(3):
+            np.testing.assert_array_equal(pops[k], runs["tma"][k], err_msg=name)
