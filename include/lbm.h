@@ -64,8 +64,9 @@ typedef enum {
 typedef enum {
     LBM_FP32 = 0, /* populations stored as FP32 */
     LBM_FP16 = 1  /* populations stored as FP16 deviations from the lattice
-                     weight times the node's own density, that density
-                     rounded to FP16 and kept in a moment plane */
+                     weight times a per-node FP16 reference (the node's own
+                     rest population per weight, kept in a moment plane);
+                     the rest deviation closes each node's mass */
 } lbm_precision;
 
 /* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,

@@ -1016,9 +1016,10 @@ extern "C" lbm_status lbm_autotune(lbm_handle *h, int32_t steps,
         return cudaStreamSynchronize(h->stream);
     };
     struct Cand { bool tma; int tx, ty; };
-    const Cand cands[] = {{true, 32, 16}, {true, 32, 8}, {true, 64, 4},
-                          {true, 64, 8},  {true, 32, 4}, {false, 32, 8},
-                          {false, 32, 4}, {false, 64, 4}};
+    const Cand cands[] = {{true, 32, 16}, {true, 32, 8},  {true, 64, 4},
+                          {true, 64, 8},  {true, 32, 4},  {true, 128, 4},
+                          {false, 32, 8}, {false, 32, 4}, {false, 64, 4},
+                          {false, 128, 4}};
     const Cand orig = {h->use_tma, h->tx, h->ty};
     Cand best = orig;
     double best_ms = 1e300;

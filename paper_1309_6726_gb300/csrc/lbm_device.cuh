@@ -125,6 +125,12 @@ struct StepArgs {
 
 constexpr int GHOST = 2;  // ghost rows on each side in y
 
+// FP16 storage keeps deviations multiplied by 2^10, an exact scaling that
+// lifts the minority component's small deviations out of FP16's subnormal
+// range (|deviation| stays far below FP16's 65504 / 2^10 = 64).
+constexpr float kDevScale = 1024.0f;
+constexpr float kInvDevScale = 1.0f / 1024.0f;
+
 // Offsets of the ghost copies of row y (0 or 1, or ny - 2 or ny - 1):
 // returns how many (0, 1 or 2; 2 only when ny < 4) and writes them to g[].
 __device__ __forceinline__ int ghost_rows(int y, int ny, int pitch, int own,

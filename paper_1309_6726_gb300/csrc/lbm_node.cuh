@@ -16,16 +16,17 @@ namespace lbmk {
 // Store32: plain FP32 planes.
 //
 // Store16: population i of a node is kept as the FP16 number
-//   d_i = (f_i - w_i * rho~) / w_i,
-// with rho~ the node's own (post-collision) component density rounded to
-// FP16 and stored once per node in a moment plane; the solute likewise as
-// d_j = 4 g_j - C~.  Reading rebuilds f_i = w_i (rho~ + d_i) in FP32.  The
-// deviation is small next to rho (it carries velocity and non-equilibrium
-// parts only), so FP16's relative precision applies to a quantity ~10-100x
-// smaller than f_i itself; the minority component (rho ~ 0.006) keeps the
-// same relative accuracy as the majority because rho~ is local.  Writing
-// divides by the same FP32 weights the reading multiplies by, so the
-// weights' rounding cancels.
+//   d_i = 2^10 (f_i - w_i * rho~) / w_i,
+// with rho~ a per-node reference rounded to FP16 and stored once per node in
+// a moment plane: rho~ = f_0 / w_0, the node's own post-collision rest
+// population per weight (close to its density).  The solute likewise as
+// d_j = 2^10 (4 g_j - C~) with C~ its concentration.  Reading rebuilds
+// f_i = w_i (rho~ + 2^-10 d_i) in FP32.  The deviation is small next to rho (it
+// carries velocity and non-equilibrium parts only), so FP16's relative
+// precision applies to a quantity ~10-100x smaller than f_i itself; the
+// minority component (rho ~ 0.006) keeps the same relative accuracy as the
+// majority because rho~ is local.  The rest deviation absorbs the rounding
+// of the eight others so that each node's stored mass equals its FP32 mass.
 // ---------------------------------------------------------------------------
 
 struct Store32 {
@@ -96,12 +97,26 @@ __device__ __forceinline__ void store9(typename S::T *__restrict__ p,
         float r = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) r += f[i];
-        const __half rh = __float2half_rn(r);
+        // Reference rho~ = f_0 / w_0 rounded to FP16 (the density times
+        // 1 - 3/2 u.u at equilibrium): every deviation is small, and the
+        // rest population's is ~0.  The eight moving deviations are rounded
+        // first; the rest population then carries what the readers'
+        // reconstruction of them (w_i (rho~ + d_i), rounded exactly as
+        // readers do) leaves of the density r, so rounding creates no mass.
+        const __half rh = __float2half_rn(f[0] * (1.0f / wq(0)));
         const float rt = __half2float(rh);
         *mp = rh;
+        float moving = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            p[i * plane] = __float2half_rn(f[i] * (1.0f / wq(i)) - rt);
+        for (int i = 1; i < Q; ++i) {
+            const __half dh = __float2half_rn((f[i] * (1.0f / wq(i)) - rt) * kDevScale);
+            p[i * plane] = dh;
+            moving += __fmul_rn(wq(i), __fmaf_rn(__half2float(dh), kInvDevScale, rt));
+        }
+        // divide by the FP32 weight the readers multiply by: with the
+        // rounded reciprocal instead, w_0 * (1 / w_0) = 1 + 7.45e-9 would
+        // bias the rest population up by that much every step
+        p[0] = __float2half_rn((__fdiv_rn(r - moving, wq(0)) - rt) * kDevScale);
     }
 }
 
@@ -118,7 +133,7 @@ __device__ __forceinline__ void store4(typename S::T *__restrict__ p,
         const float ct = __half2float(ch);
         *mp = ch;
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[k * plane] = __float2half_rn(4.0f * g[k] - ct);
+        for (int k = 0; k < QS; ++k) p[k * plane] = __float2half_rn((4.0f * g[k] - ct) * kDevScale);
     }
 }
 

@@ -67,7 +67,7 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
-            f[i] = __fmul_rn(wq(i), __fadd_rn(rt, dv));  // no fusing (see TMA kernel)
+            f[i] = __fmul_rn(wq(i), __fmaf_rn(dv, kInvDevScale, rt));  // see TMA kernel
         }
     }
 }
@@ -93,7 +93,7 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
-            g[k] = __fmul_rn(0.25f, __fadd_rn(ct, dv));
+            g[k] = __fmul_rn(0.25f, __fmaf_rn(dv, kInvDevScale, ct));
         }
     }
 }
@@ -234,6 +234,7 @@ cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
     if (tx == 32 && ty == 16) return launch_tile<32, 16>(a, ntiles, half, s);
     if (tx == 64 && ty == 4) return launch_tile<64, 4>(a, ntiles, half, s);
     if (tx == 64 && ty == 8) return launch_tile<64, 8>(a, ntiles, half, s);
+    if (tx == 128 && ty == 4) return launch_tile<128, 4>(a, ntiles, half, s);
     return cudaErrorInvalidValue;
 }
 

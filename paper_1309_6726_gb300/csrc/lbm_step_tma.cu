@@ -156,8 +156,9 @@ __device__ __forceinline__ void spull9(const typename S::T *tile,
             // explicit roundings: no fused multiply-add may merge this
             // product into a later sum, so every pull of a node's
             // population (own node or density ring) gives the same bits
-            f[i] = __fmul_rn(wq(i), __fadd_rn(__half2float(mom[comp * TT::PL + cell]),
-                                              __half2float(tile[q * TT::PL + cell])));
+            f[i] = __fmul_rn(wq(i), __fmaf_rn(__half2float(tile[q * TT::PL + cell]),
+                                              kInvDevScale,
+                                              __half2float(mom[comp * TT::PL + cell])));
         }
     }
 }
@@ -174,8 +175,9 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
         if constexpr (!S::kHalf) {
             g[k] = tile[q * TT::PL + cell];
         } else {
-            g[k] = __fmul_rn(0.25f, __fadd_rn(__half2float(mom[2 * TT::PL + cell]),
-                                              __half2float(tile[q * TT::PL + cell])));
+            g[k] = __fmul_rn(0.25f, __fmaf_rn(__half2float(tile[q * TT::PL + cell]),
+                                              kInvDevScale,
+                                              __half2float(mom[2 * TT::PL + cell])));
         }
     }
 }
@@ -439,7 +441,7 @@ static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
     return cudaGetLastError();
 }
 
-#define LBM_TMA_SHAPES(M) M(32, 8) M(32, 4) M(64, 4) M(32, 16) M(64, 8)
+#define LBM_TMA_SHAPES(M) M(32, 8) M(32, 4) M(64, 4) M(32, 16) M(64, 8) M(128, 4)
 
 // Persistent grid of the TMA step kernel for a tile shape (also sets its
 // shared-memory limit); 0 on an unsupported shape.

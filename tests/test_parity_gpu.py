@@ -282,3 +282,27 @@ def test_variants_graphs_and_autotune_bit_identical(monkeypatch, precision):
     for name, pops in runs.items():
         for k in range(3):
             np.testing.assert_array_equal(pops[k], runs["tma"][k], err_msg=name)
+
+
+def test_preform_small_fp32_and_fp16():
+    # A 192 x 192 synthetic preform (discs, lognormal radii, porosity 0.5 in
+    # the middle band) with the reactive model: FP32 parity with the oracle
+    # element by element, FP16 within its stated bound, masks exact.
+    geom = I.preform(n=192, seed=7, x_res=24, x_out=24)
+    mp = I.ModelParams(g_ads=I.G_ADS_30, k_r=5e-3, m_threshold=0.05, inlet=1)
+    o = oracle_for(geom, mp)
+    s32 = lbm.Solver(geom, mp, "fp32")
+    s16 = lbm.Solver(geom, mp, "fp16")
+    for n in (40, 80):
+        o.step(n)
+        s32.step(n)
+        s16.step(n)
+        np.testing.assert_array_equal(s32.solid_mask(), o.solid())
+        np.testing.assert_array_equal(s16.solid_mask(), o.solid())
+        fo = oracle_pops(o)
+        assert pop_error(s32.populations(), fo) < FP32_TOL
+        assert pop_error(s16.populations(), fo) < FP16_TOL_LONG
+    assert (o.solid() != geom.solid).sum() > 0
+    g32 = s32.observables()[0]
+    led = o.ledger()
+    assert g32["ledger_m"] == pytest.approx(led[3], rel=1e-5)
