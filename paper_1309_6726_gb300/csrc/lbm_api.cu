@@ -203,12 +203,13 @@ static bool make_maps(lbm_handle *h, std::string &why) {
         for (int l = 0; l < count; ++l) {
             const LatDesc &d = h->desc[l];
             const cuuint64_t rows = (cuuint64_t)(d.ny + 2 * GHOST);
-            cuuint64_t dims[3] = {(cuuint64_t)d.nx, rows, (cuuint64_t)NPOP};
+            cuuint64_t dims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NPOP};
             cuuint64_t strides[2] = {(cuuint64_t)d.pitch * esz, (cuuint64_t)d.plane * esz};
             cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx, h->half),
                                  (cuuint32_t)(h->ty + 4), (cuuint32_t)NPOP};
             cuuint32_t es[3] = {1, 1, 1};
-            void *base = (char *)h->d_pop[b] + (size_t)(d.pop_off - GHOST * d.pitch) * esz;
+            void *base = (char *)h->d_pop[b] +
+                         (size_t)(d.pop_off - GHOST * d.pitch - XGHOST) * esz;
             CUresult r = enc(&maps[b * count + l],
                              h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -223,9 +224,10 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                 return false;
             }
             if (h->half) {
-                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, rows, (cuuint64_t)NMOM};
+                cuuint64_t mdims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NMOM};
                 cuuint32_t mbox[3] = {box[0], box[1], (cuuint32_t)NMOM};
-                void *mbase = (char *)h->d_mom[b] + (size_t)(d.mom_off - GHOST * d.pitch) * 2;
+                void *mbase = (char *)h->d_mom[b] +
+                              (size_t)(d.mom_off - GHOST * d.pitch - XGHOST) * 2;
                 r = enc(&moms[b * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                         mbase, mdims, strides, mbox, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -242,12 +244,13 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     std::vector<CUtensorMap> mmaps(count);
     for (int l = 0; l < count; ++l) {
         const LatDesc &d = h->desc[l];
-        cuuint64_t dims[2] = {(cuuint64_t)d.nx, (cuuint64_t)(d.ny + 2 * GHOST)};
+        cuuint64_t dims[2] = {(cuuint64_t)d.pitch, (cuuint64_t)(d.ny + 2 * GHOST)};
         cuuint64_t strides[1] = {(cuuint64_t)d.pitch};
         cuuint32_t box[2] = {(cuuint32_t)tma_mask_box_x(h->tx), (cuuint32_t)(h->ty + 4)};
         cuuint32_t es[2] = {1, 1};
         CUresult r = enc(&mmaps[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                         h->d_mask + d.node_off - GHOST * d.pitch, dims, strides, box, es,
+                         h->d_mask + d.node_off - GHOST * d.pitch - XGHOST, dims,
+                         strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -393,7 +396,8 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
                         "lattice " + std::to_string(l) +
                             ": need nx >= 1, ny >= 3 and all arrays");
         // 32-bit offsets inside a lattice: 22 planes of ny * pitch elements
-        if ((int64_t)NPOP * (G.ny + 2 * GHOST) * ((G.nx + 31) / 32 * 32) >= ((int64_t)1 << 31))
+        if ((int64_t)NPOP * (G.ny + 2 * GHOST) * ((G.nx + 2 * XGHOST + 31) / 32 * 32) >=
+            ((int64_t)1 << 31))
             return fail(nullptr, LBM_EINVAL, "lattice too large");
         if (!(0 <= G.cap_x0 && G.cap_x0 < G.cap_x1 && G.cap_x1 <= G.nx))
             return fail(nullptr, LBM_EINVAL,
@@ -421,7 +425,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         LatDesc &d = h->desc[l];
         d.nx = G.nx;
         d.ny = G.ny;
-        d.pitch = (G.nx + 31) / 32 * 32;
+        d.pitch = (G.nx + 2 * XGHOST + 31) / 32 * 32;
         d.tiles_x = (G.nx + h->tx - 1) / h->tx;
         d.tile_base = tiles;
         tiles += d.tiles_x * ((G.ny + h->ty - 1) / h->ty);
@@ -430,9 +434,9 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.inlet = P.inlet ? 1 : 0;
         // planes include GHOST rows on both sides; offsets point at row 0
         d.plane = (int64_t)(d.ny + 2 * GHOST) * d.pitch;
-        d.node_off = node + GHOST * d.pitch;
-        d.pop_off = pop + GHOST * d.pitch;
-        d.mom_off = mom + GHOST * d.pitch;
+        d.node_off = node + GHOST * d.pitch + XGHOST;
+        d.pop_off = pop + GHOST * d.pitch + XGHOST;
+        d.mom_off = mom + GHOST * d.pitch + XGHOST;
         d.col_off = sec;
         node += d.plane;
         pop += NPOP * d.plane;
@@ -473,10 +477,12 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         for (int x = 0; x < d.nx; ++x) col_lat[h->col_base[l] + x] = l;
         const uint8_t *S = g[l].solid;
         for (int y = -GHOST; y < d.ny + GHOST; ++y) {
-            const int ys = (y + d.ny) % d.ny;  // row y or its periodic image
-            for (int x = 0; x < d.nx; ++x)
+            const int ys = ((y % d.ny) + d.ny) % d.ny;  // periodic image
+            for (int x = -GHOST; x < d.nx + GHOST; ++x) {
+                const int xs = ((x % d.nx) + d.nx) % d.nx;
                 mask[d.node_off + (int64_t)y * d.pitch + x] =
-                    S[(int64_t)ys * d.nx + x] ? 7 : 0;
+                    S[(int64_t)ys * d.nx + xs] ? 7 : 0;
+            }
         }
         for (int x = d.cap_x0; x < d.cap_x1; ++x) {
             int fl = 0, b = 0, t = 0;

@@ -133,8 +133,8 @@ __global__ void k_unstream(const LatDesc *desc, int l, const float *canon,
         v[2 * Q + k] = canon[(2 * Q + (b ? sopp(k) : k)) * P + src];
     }
     store_node(fout, mout, d, half, own, v);
-    if (y < GHOST) store_node(fout, mout, d, half, own + (int64_t)d.ny * d.pitch, v);
-    if (y >= d.ny - GHOST) store_node(fout, mout, d, half, own - (int64_t)d.ny * d.pitch, v);
+    for_ghosts(x, y, d.nx, d.ny, d.pitch, (int)own,
+               [&](int off) { store_node(fout, mout, d, half, off, v); });
 }
 
 // Post-streaming fields of lattice l at step t into canon ([22][ny][nx]);
@@ -210,7 +210,7 @@ __global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
     const MaskBits mb(t);
     uint8_t *mask = mask_all + d.node_off;
     const int64_t own = (int64_t)y * d.pitch + x;
-    mask_store(mask, (int)own, y, d.ny, d.pitch, (mask[own] & mb.force) ? 7 : 0);
+    mask_store(mask, (int)own, x, y, d.nx, d.ny, d.pitch, (mask[own] & mb.force) ? 7 : 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -8,12 +8,14 @@
 //     starts on a 128-byte boundary in FP32 storage);
 //   FP16 storage adds 3 moment planes per lattice and buffer (rho_A,
 //     rho_B, C rounded to FP16) that the deviations are taken from;
-//   every plane (populations, moments, mask) has two ghost rows above and
-//     below the lattice, rows -2, -1 and ny, ny + 1, holding copies of rows
-//     ny - 2, ny - 1 and 0, 1 (the periodic images): the offsets below point
-//     at row 0, so row y of a plane is at offset y * pitch for -2 <= y <
-//     ny + 2, and the nodes next to the y boundaries refresh the copies
-//     whenever they write;
+//   every plane (populations, moments, mask) has a two-node ghost band
+//     around the lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx,
+//     nx + 1 -- holding the periodic images of the nodes next to the
+//     boundaries; the offsets below point at logical node (0, 0), which
+//     sits at physical row 2 and column 16 of the lattice's planes, so node
+//     (x, y) is at offset y * pitch + x for -2 <= x < nx + 2,
+//     -2 <= y < ny + 2; the nodes next to the boundaries refresh their
+//     images whenever they write;
 //   mask: one byte per node, read and written in place (see MaskBits);
 //   deposit: one double per node;
 //   per section column: fluid-node counter (closure), initial wall
@@ -75,7 +77,7 @@ struct MaskBits {
 // One lattice of the batch (128 bytes: the TMA step kernel bulk-copies it
 // into shared memory next to each tile).
 struct alignas(16) LatDesc {
-    int32_t nx, ny, pitch, tiles_x;
+    int32_t nx, ny, pitch, tiles_x;  // pitch >= nx + 2 * XGHOST
     int32_t tile_base, cap_x0, cap_x1, inlet;
     int64_t node_off;   // first node of this lattice in mask / deposit
     int64_t pop_off;    // first element of plane 0 in a population buffer
@@ -131,22 +133,33 @@ constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
 
-// Offsets of the ghost copies of row y (0 or 1, or ny - 2 or ny - 1):
-// returns how many (0, 1 or 2; 2 only when ny < 4) and writes them to g[].
-__device__ __forceinline__ int ghost_rows(int y, int ny, int pitch, int own,
-                                          int g[2]) {
-    int n = 0;
-    if (y < GHOST) g[n++] = own + ny * pitch;
-    if (y >= ny - GHOST) g[n++] = own - ny * pitch;
-    return n;
+constexpr int XGHOST = 16;  // physical columns before logical column 0
+
+// Calls f(offset) for every periodic image of node (x, y) that lies in the
+// ghost band (columns -2 .. nx + 1, rows -2 .. ny + 1, the node itself
+// excluded); nodes at least two nodes inside the lattice have none.
+template <class F>
+__device__ __forceinline__ void for_ghosts(int x, int y, int nx, int ny,
+                                           int pitch, int own, F f) {
+    if (x >= GHOST && x < nx - GHOST && y >= GHOST && y < ny - GHOST) return;
+    for (int ky = -2; ky <= 2; ++ky) {
+        const int yi = y + ky * ny;
+        if (yi < -GHOST || yi >= ny + GHOST) continue;
+        for (int kx = -2; kx <= 2; ++kx) {
+            if (kx == 0 && ky == 0) continue;
+            const int xi = x + kx * nx;
+            if (xi < -GHOST || xi >= nx + GHOST) continue;
+            f(own + ky * ny * pitch + kx * nx);
+        }
+    }
 }
 
-// Stores a mask byte of row y and its ghost copies.
-__device__ __forceinline__ void mask_store(uint8_t *mask, int own, int y,
-                                           int ny, int pitch, uint8_t v) {
+// Stores a mask byte of node (x, y) and its ghost images.
+__device__ __forceinline__ void mask_store(uint8_t *mask, int own, int x,
+                                           int y, int nx, int ny, int pitch,
+                                           uint8_t v) {
     mask[own] = v;
-    if (y < GHOST) mask[own + ny * pitch] = v;
-    if (y >= ny - GHOST) mask[own - ny * pitch] = v;
+    for_ghosts(x, y, nx, ny, pitch, own, [&](int off) { mask[off] = v; });
 }
 
 // Periodic index for any offset (lattices smaller than a tile included).

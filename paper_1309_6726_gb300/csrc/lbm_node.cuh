@@ -230,9 +230,9 @@ __device__ __forceinline__ bool fluid_update(
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
     store_node22<S>(a, d, own, fA, fB, g);
-    // ghost copies of rows next to the y boundaries
-    if (gy < GHOST) store_node22<S>(a, d, own + d.ny * d.pitch, fA, fB, g);
-    if (gy >= d.ny - GHOST) store_node22<S>(a, d, own - d.ny * d.pitch, fA, fB, g);
+    // periodic images in the ghost band
+    for_ghosts(gx, gy, d.nx, d.ny, d.pitch, own,
+               [&](int off) { store_node22<S>(a, d, off, fA, fB, g); });
     return flagged;
 }
 

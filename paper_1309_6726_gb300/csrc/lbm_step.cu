@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TX *TY)
                 pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
                 retire_node(a, d, l, own, fA, fB, g);
             }
-            if (nb != s_own) mask_store(mask, own, gy, ny, d.pitch, nb);
+            if (nb != s_own) mask_store(mask, own, gx, gy, nx, ny, d.pitch, nb);
         } else {
             float g[QS], rAn[Q], rBn[Q];
             unsigned snb = 0;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TX *TY)
             pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
             const bool flagged = fluid_update<S>(a, d, l, t, gx, gy, own, fA, fB, g,
                                                  rAn, rBn, snb, ns);
-            if (flagged) mask_store(mask, own, gy, ny, d.pitch, s_own | mb.next);
+            if (flagged) mask_store(mask, own, gx, gy, nx, ny, d.pitch, s_own | mb.next);
         }
     }
     finish_launch(a, t);

@@ -14,9 +14,9 @@
 //     one is computed;
 //   * all pulls -- the tile's own nodes and the one-node density ring the
 //     cohesion stencil needs -- then read shared memory at fixed offsets;
-//   * halo cells outside the lattice (the copy fills them with zeros) are
-//     patched with their periodic images by plain loads, only on tiles that
-//     touch a lattice edge;
+//   * the lattice planes carry a two-node periodic ghost band (rows and
+//     columns), so every copy reads valid neighbours and nothing needs
+//     patching;
 //   * every wait on an mbarrier is bounded; on time-out the kernel records
 //     an error, lets its copies in flight land and returns.
 #include <cuda.h>
@@ -238,8 +238,9 @@ __global__ void __launch_bounds__(TX *TY)
         const LatDesc *gd = a.desc + l;
         const int local = tile - gd->tile_base;
         const int tiles_x = gd->tiles_x;
-        const int x0 = (local % tiles_x) * TX;
-        const int y0 = (local / tiles_x) * TY;  // row ty0 - 2 of the plane
+        // physical coordinates: column x0 - XO and row ty0 - 2 of the lattice
+        const int x0 = (local % tiles_x) * TX + XGHOST;
+        const int y0 = (local / tiles_x) * TY;
         fence_proxy_async();
         mbar_expect_tx(&bar[s], TT::TX_BYTES);
         bulk_load(sdesc(slot), gd, 128, &bar[s]);
@@ -285,45 +286,12 @@ __global__ void __launch_bounds__(TX *TY)
         const int local = tile - d.tile_base;
         const int tx0 = (local % d.tiles_x) * TX;
         const int ty0 = (local / d.tiles_x) * TY;
-        // rows come from the ghost rows near the y boundaries; only tiles
-        // at the x ends need the periodic images of halo columns
-        const bool edge = tx0 < 2 || tx0 + TX + 2 > nx;
+        // rows / columns of the tile that hold lattice nodes; frame
+        // positions further out are never a node's neighbour
+        const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
         T *tp = stage_pop(s);
         __half *tm = stage_mom(s);
         uint8_t *sm = stage_mask(s);
-
-        // periodic images of halo columns outside the lattice (the copies
-        // filled them with zeros); one thread per such cell, all planes;
-        // cells spread over the warps
-        // rows / columns of the tile that hold lattice nodes; the frame
-        // needs one more around them and the pulls of the frame one more
-        const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
-        if (edge) {
-            const T *__restrict__ src = fin + d.pop_off;
-            const uint8_t *__restrict__ msrc = a.mask + d.node_off;
-            const int CW = m_act + 4;   // columns read: x0 - 2 .. x0 + m_act + 1
-            const int RH = n_act + 4;   // rows read: y0 - 2 .. y0 + n_act + 1
-            for (int j = 0; j * TT::NT < RH * CW; ++j) {
-                const int e = j * TT::NT + lane * TT::NW + warp;
-                if (e >= RH * CW) continue;
-                const int yy = e / CW;
-                const int xc = e - yy * CW - 2;  // column relative to x0
-                const int gy = ty0 - 2 + yy, gx = tx0 + xc;  // gy: -2 .. ny + 1
-                if (gx >= 0 && gx < nx) continue;
-                const int g = gy * d.pitch + wrapg(gx, nx);
-                const int cell = yy * TT::BX + xc + TT::XO;
-#pragma unroll 2
-                for (int q = 0; q < NPOP; ++q)
-                    tp[q * TT::PL + cell] = src[(int64_t)q * d.plane + g];
-                if constexpr (S::kHalf) {
-#pragma unroll
-                    for (int q = 0; q < NMOM; ++q)
-                        tm[q * TT::PL + cell] = a.min_[d.mom_off + (int64_t)q * d.plane + g];
-                }
-                sm[yy * TT::MBX + xc + TT::MXO] = msrc[g];
-            }
-            __syncthreads();
-        }
 
         // own node: mask bits, pull, density
         const int lx = tid % TX, ly = tid / TX;
@@ -391,7 +359,7 @@ __global__ void __launch_bounds__(TX *TY)
             if (s_own & mb.force) {
                 if (own_pull_fluid) retire_node(a, d, l, own, fA, fB, g);
                 const uint8_t nb = s_own | mb.next;
-                if (nb != s_own) mask_store(a.mask + d.node_off, own, y, ny, d.pitch, nb);
+                if (nb != s_own) mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, nb);
             } else {
                 float rAn[Q], rBn[Q];
 #pragma unroll
@@ -404,7 +372,7 @@ __global__ void __launch_bounds__(TX *TY)
                 const bool flagged = fluid_update<S>(a, d, l, t, x, y, own, fA, fB, g,
                                                      rAn, rBn, snb, ns);
                 if (flagged)
-                    mask_store(a.mask + d.node_off, own, y, ny, d.pitch, s_own | mb.next);
+                    mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, s_own | mb.next);
             }
         }
     }
