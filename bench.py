@@ -114,15 +114,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(name: str, rank: int = 0):
+def build_workload(name: str, rank: int = 0, lattices: int = 512):
     from paper_1309_6726_gb300 import inputs as I
     if name == "sweep":
-        members = I.sweep_members(512, seed=1236 + 1000 * rank)
+        members = I.sweep_members(512, seed=1236 + 1000 * rank)[:lattices]
         pairs = [I.sweep_lattice(m) for m in members]
         geoms = [g for g, _ in pairs]
         params = [p for _, p in pairs]
-        desc = ("batched sweep: 512 capillaries, W 16-128, L 1024-4096, "
-                "k_r logU[1e-5,1e-2], theta 20-60 deg, tau_A/tau_B 0.6-1.5")
+        desc = ("batched sweep: %d capillaries, W 16-128, L 1024-4096, "
+                "k_r logU[1e-5,1e-2], theta 20-60 deg, tau_A/tau_B 0.6-1.5"
+                % len(geoms))
     elif name == "paper":
         g, p, _ = I.config_paper_scale(k_r=1e-3)
         geoms, params = [g], [p]
@@ -287,6 +288,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattices", type=int, default=512,
+                    help="sweep only: the first N capillaries (a smaller "
+                         "case for profiling; the benchmark is N = 512)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -308,7 +312,7 @@ def main():
         torch.distributed.barrier()
     __graft_entry__.build()
 
-    geoms, params, desc = build_workload(args.workload, rank)
+    geoms, params, desc = build_workload(args.workload, rank, args.lattices)
     n_fluid = fluid_nodes(geoms)
     n_all = all_nodes(geoms)
     f_s = surface_fraction(geoms)
@@ -342,7 +346,7 @@ def main():
     bpn = BYTES_PER_NODE[args.precision] + DEPOSIT_BYTES * f_s
     achieved = n_fluid * bpn / (ms_step / 1e3) / 1e9
     e2e = None
-    if rank == 0:
+    if rank == 0 and args.e2e_steps > 0:
         dt, h2d, d2h = time_e2e(geoms, params, args.precision, args.e2e_steps,
                                 observe_every=10)
         e2e = {"value": n_fluid * args.e2e_steps / dt / 1e9 * world,

@@ -22,7 +22,7 @@ cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
                                int ty, bool half, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
-                            const CUtensorMap *mask_maps, const int *sched,
+                            const CUtensorMap *mask_maps, const TileRec *sched,
                             int nslots, int grid, int tx, int ty, bool half,
                             int *err, cudaStream_t s);
 cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
@@ -87,7 +87,7 @@ struct lbm_handle {
     CUtensorMap *d_maps = nullptr;     // [2 buffers][count] population maps
     CUtensorMap *d_mom_maps = nullptr; // [2 buffers][count] FP16 moment maps
     CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
-    int *d_sched = nullptr;            // TMA kernel: tiles of each block
+    TileRec *d_sched = nullptr;        // TMA kernel: tiles of each block
     int sched_grid = 0, sched_slots = 0;
     cudaGraphExec_t graph = nullptr;   // kGraphSteps steps from cur == 0
     bool use_graph = true;
@@ -285,7 +285,8 @@ static bool make_maps(lbm_handle *h, std::string &why) {
 // Tile schedule of the persistent TMA kernel: the tile columns ("strips")
 // of every lattice are dealt to the `grid` blocks, each to the block with
 // the least work so far (longest strips first); block b then walks its
-// strips top to bottom, its k-th tile at sched[b + k * grid] (-1 = done).
+// strips top to bottom, its k-th tile at sched[b + k * grid] (lattice -1 =
+// done).
 static bool make_schedule(lbm_handle *h, std::string &why) {
     int grid = 0;
     cudaError_t e = grid_step_tma(h->tx, h->ty, h->half, &grid);
@@ -302,7 +303,7 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
     }
     std::stable_sort(strips.begin(), strips.end(),
                      [](const Strip &a, const Strip &b) { return a.rows > b.rows; });
-    std::vector<std::vector<int>> lists(grid);
+    std::vector<std::vector<TileRec>> lists(grid);
     std::vector<long long> load(grid, 0);
     // blocks ordered by load with a simple binary heap
     std::vector<int> heap(grid);
@@ -312,19 +313,18 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
     for (const Strip &st : strips) {
         std::pop_heap(heap.begin(), heap.end(), less);
         const int b = heap.back();
-        const LatDesc &d = h->desc[st.lat];
         for (int r = 0; r < st.rows; ++r)
-            lists[b].push_back(d.tile_base + r * d.tiles_x + st.col);
+            lists[b].push_back(TileRec{st.lat, st.col * h->tx, r * h->ty, 0});
         load[b] += st.rows;
         std::push_heap(heap.begin(), heap.end(), less);
     }
     size_t slots = 0;
     for (auto &v : lists) slots = std::max(slots, v.size());
-    std::vector<int> sched((size_t)grid * slots, -1);
+    std::vector<TileRec> sched((size_t)grid * slots, TileRec{-1, 0, 0, 0});
     for (int b = 0; b < grid; ++b)
         for (size_t k = 0; k < lists[b].size(); ++k) sched[b + k * grid] = lists[b][k];
-    if (cudaMalloc(&h->d_sched, std::max<size_t>(sched.size(), 1) * sizeof(int)) != cudaSuccess ||
-        cudaMemcpy(h->d_sched, sched.data(), sched.size() * sizeof(int),
+    if (cudaMalloc(&h->d_sched, std::max<size_t>(sched.size(), 1) * sizeof(TileRec)) != cudaSuccess ||
+        cudaMemcpy(h->d_sched, sched.data(), sched.size() * sizeof(TileRec),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
         why = "schedule upload";
         return false;

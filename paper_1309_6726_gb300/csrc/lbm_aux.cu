@@ -19,8 +19,7 @@ __device__ __forceinline__ float load_pop(const void *base, const __half *mom,
     const float dv = __half2float(static_cast<const __half *>(base)[d.pop_off + q * d.plane + e]);
     const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
     const float rt = __half2float(mom[d.mom_off + comp * d.plane + e]);
-    return comp < 2 ? __fmul_rn(wq(q - comp * Q), __fmaf_rn(dv, kInvDevScale, rt))
-                    : __fmul_rn(0.25f, __fmaf_rn(dv, kInvDevScale, rt));
+    return comp < 2 ? dec_pop(q - comp * Q, dv, rt) : dec_sol(dv, rt);
 }
 
 // Post-streaming populations of node (x, y) at the current step: 22 values
@@ -58,30 +57,13 @@ __device__ __forceinline__ void store_node(void *fout, __half *mout,
         return;
     }
     __half *f = static_cast<__half *>(fout);
+    __half dq[Q];
     for (int comp = 0; comp < 2; ++comp) {
-        float r = 0.f;
-        for (int i = 0; i < Q; ++i) r += v[comp * Q + i];
-        // same reference and mass-closing rest population as the step kernels
-        const __half rh = __float2half_rn(v[comp * Q] * (1.0f / wq(0)));
-        const float rt = __half2float(rh);
-        mout[d.mom_off + comp * d.plane + own] = rh;
-        float moving = 0.f;
-        for (int i = 1; i < Q; ++i) {
-            const __half dh =
-                __float2half_rn((v[comp * Q + i] * (1.0f / wq(i)) - rt) * kDevScale);
-            f[d.pop_off + (comp * Q + i) * d.plane + own] = dh;
-            moving += __fmul_rn(wq(i), __fmaf_rn(__half2float(dh), kInvDevScale, rt));
-        }
-        f[d.pop_off + (comp * Q) * d.plane + own] =
-            __float2half_rn((__fdiv_rn(r - moving, wq(0)) - rt) * kDevScale);
+        mout[d.mom_off + comp * d.plane + own] = enc9(v + comp * Q, dq);
+        for (int i = 0; i < Q; ++i) f[d.pop_off + (comp * Q + i) * d.plane + own] = dq[i];
     }
-    const float c = v[18] + v[19] + v[20] + v[21];
-    const __half ch = __float2half_rn(c);
-    const float ct = __half2float(ch);
-    mout[d.mom_off + 2 * d.plane + own] = ch;
-    for (int k = 0; k < QS; ++k)
-        f[d.pop_off + (2 * Q + k) * d.plane + own] =
-            __float2half_rn((4.0f * v[18 + k] - ct) * kDevScale);
+    mout[d.mom_off + 2 * d.plane + own] = enc4(v + 2 * Q, dq);
+    for (int k = 0; k < QS; ++k) f[d.pop_off + (2 * Q + k) * d.plane + own] = dq[k];
 }
 
 // canonical layout of one lattice: [22][ny][nx] floats, no padding.

@@ -92,6 +92,12 @@ struct alignas(16) LatDesc {
 };
 static_assert(sizeof(LatDesc) == 128, "LatDesc is copied as 128 bytes");
 
+// One tile of the persistent TMA kernel's schedule: its lattice (-1 ends a
+// block's list) and its first logical column and row.
+struct alignas(16) TileRec {
+    int32_t lat, x0, y0, pad;
+};
+
 struct LatState {
     double ledger[4];               // A, B, solute, deposit moved by growth
     unsigned long long closure;     // first closure step count, ~0 if none
@@ -127,11 +133,78 @@ struct StepArgs {
 
 constexpr int GHOST = 2;  // ghost rows on each side in y
 
-// FP16 storage keeps deviations multiplied by 2^10, an exact scaling that
-// lifts the minority component's small deviations out of FP16's subnormal
-// range (|deviation| stays far below FP16's 65504 / 2^10 = 64).
+// ---- FP16 storage codec ------------------------------------------------------
+// A component's populations are kept as FP16 deviations from a per-node
+// reference rho~ (FP16, stored once per node and component):
+//   moving i = 1..8:  d = 2^10 (f_i / w_i - rho~),  f_i = w_i (rho~ + 2^-10 d)
+//   rest:             d = 2^12 (f_0 - w_0 rho~),    f_0 = w_0 rho~ + 2^-12 d
+//   solute k = 0..3:  d = 2^10 (4 g_k - C~),        g_k = (C~ + 2^-10 d) / 4
+// The power-of-two scales are exact; they lift the minority component's
+// small deviations out of FP16's subnormal range (|d| stays far below
+// 65504).  The rest population's scale is a power of two rather than a
+// weight so that the writer can solve for it without a division.  Every
+// read rounds exactly as written here (no contraction into later sums), so
+// all code paths rebuild the same FP32 value from the same bits.
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
+constexpr float kRestScale = 4096.0f;
+constexpr float kInvRestScale = 1.0f / 4096.0f;
+
+// Population i (0..8) of a D2Q9 component from its deviation and reference.
+__device__ __forceinline__ float dec_pop(int i, float d, float rt) {
+    return i == 0 ? __fmaf_rn(d, kInvRestScale, __fmul_rn(wq(0), rt))
+                  : __fmul_rn(wq(i), __fmaf_rn(d, kInvDevScale, rt));
+}
+// A solute population from its deviation and reference.
+__device__ __forceinline__ float dec_sol(float d, float ct) {
+    return __fmul_rn(0.25f, __fmaf_rn(d, kInvDevScale, ct));
+}
+
+// Encodes the 9 post-collision populations of one component; returns the
+// reference.  rho~ = f_0 / w_0 rounded to FP16 (the density times
+// 1 - 3/2 u.u at equilibrium), so every deviation is small.  The eight
+// moving deviations are rounded first; the rest deviation then carries
+// what their read-back values leave of the FP32 density, so rounding
+// creates no mass.
+__device__ __forceinline__ __half enc9(const float f[Q], __half dq[Q]) {
+    float r = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r += f[i];
+    const __half rh = __float2half_rn(f[0] * (1.0f / wq(0)));
+    const float rt = __half2float(rh);
+    const float nrt = -kDevScale * rt;
+    float moving = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        dq[i] = __float2half_rn(__fmaf_rn(f[i], kDevScale / wq(i), nrt));
+        moving += dec_pop(i, __half2float(dq[i]), rt);
+    }
+    dq[0] = __float2half_rn(((r - moving) - __fmul_rn(wq(0), rt)) * kRestScale);
+    return rh;
+}
+
+// Encodes the 4 solute populations; returns the reference C~.
+__device__ __forceinline__ __half enc4(const float g[QS], __half dq[QS]) {
+    const float c = (g[0] + g[2]) + (g[1] + g[3]);
+    const __half ch = __float2half_rn(c);
+    const float ct = __half2float(ch);
+#pragma unroll
+    for (int k = 0; k < QS; ++k) dq[k] = __float2half_rn((4.0f * g[k] - ct) * kDevScale);
+    return ch;
+}
+
+// Reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32, within
+// one ulp) refined by one Newton-Raphson step for f(r) = 1/r - x,
+// r1 = r0 + r0 (1 - x r0), with the residual 1 - x r0 formed by one fused
+// multiply-add.  The approximation alone is biased enough to double the
+// drift of a long run against the FP64 solution.  Callers keep the
+// argument above 1e-30.
+__device__ __forceinline__ float rcp_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = __fmaf_rn(-x, r, 1.0f);
+    return __fmaf_rn(r, e, r);
+}
 
 constexpr int XGHOST = 16;  // physical columns before logical column 0
 

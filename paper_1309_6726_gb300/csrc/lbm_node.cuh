@@ -15,18 +15,14 @@ namespace lbmk {
 //
 // Store32: plain FP32 planes.
 //
-// Store16: population i of a node is kept as the FP16 number
-//   d_i = 2^10 (f_i - w_i * rho~) / w_i,
-// with rho~ a per-node reference rounded to FP16 and stored once per node in
-// a moment plane: rho~ = f_0 / w_0, the node's own post-collision rest
-// population per weight (close to its density).  The solute likewise as
-// d_j = 2^10 (4 g_j - C~) with C~ its concentration.  Reading rebuilds
-// f_i = w_i (rho~ + 2^-10 d_i) in FP32.  The deviation is small next to rho (it
-// carries velocity and non-equilibrium parts only), so FP16's relative
+// Store16: FP16 deviations from a per-node FP16 reference (enc9 / enc4 and
+// dec_pop / dec_sol in lbm_device.cuh).  The deviation is small next to rho
+// (it carries velocity and non-equilibrium parts only), so FP16's relative
 // precision applies to a quantity ~10-100x smaller than f_i itself; the
 // minority component (rho ~ 0.006) keeps the same relative accuracy as the
-// majority because rho~ is local.  The rest deviation absorbs the rounding
-// of the eight others so that each node's stored mass equals its FP32 mass.
+// majority because the reference is local.  The rest deviation absorbs the
+// rounding of the eight others so that each node's stored mass equals its
+// FP32 mass.
 // ---------------------------------------------------------------------------
 
 struct Store32 {
@@ -94,29 +90,10 @@ __device__ __forceinline__ void store9(typename S::T *__restrict__ p,
 #pragma unroll
         for (int i = 0; i < Q; ++i) p[i * plane] = f[i];
     } else {
-        float r = 0.f;
+        __half dq[Q];
+        *mp = enc9(f, dq);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) r += f[i];
-        // Reference rho~ = f_0 / w_0 rounded to FP16 (the density times
-        // 1 - 3/2 u.u at equilibrium): every deviation is small, and the
-        // rest population's is ~0.  The eight moving deviations are rounded
-        // first; the rest population then carries what the readers'
-        // reconstruction of them (w_i (rho~ + d_i), rounded exactly as
-        // readers do) leaves of the density r, so rounding creates no mass.
-        const __half rh = __float2half_rn(f[0] * (1.0f / wq(0)));
-        const float rt = __half2float(rh);
-        *mp = rh;
-        float moving = 0.f;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const __half dh = __float2half_rn((f[i] * (1.0f / wq(i)) - rt) * kDevScale);
-            p[i * plane] = dh;
-            moving += __fmul_rn(wq(i), __fmaf_rn(__half2float(dh), kInvDevScale, rt));
-        }
-        // divide by the FP32 weight the readers multiply by: with the
-        // rounded reciprocal instead, w_0 * (1 / w_0) = 1 + 7.45e-9 would
-        // bias the rest population up by that much every step
-        p[0] = __float2half_rn((__fdiv_rn(r - moving, wq(0)) - rt) * kDevScale);
+        for (int i = 0; i < Q; ++i) p[i * plane] = dq[i];
     }
 }
 
@@ -128,12 +105,10 @@ __device__ __forceinline__ void store4(typename S::T *__restrict__ p,
 #pragma unroll
         for (int k = 0; k < QS; ++k) p[k * plane] = g[k];
     } else {
-        const float c = (g[0] + g[2]) + (g[1] + g[3]);
-        const __half ch = __float2half_rn(c);
-        const float ct = __half2float(ch);
-        *mp = ch;
+        __half dq[QS];
+        *mp = enc4(g, dq);
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[k * plane] = __float2half_rn((4.0f * g[k] - ct) * kDevScale);
+        for (int k = 0; k < QS; ++k) p[k * plane] = dq[k];
     }
 }
 
@@ -185,16 +160,16 @@ __device__ __forceinline__ bool fluid_update(
     const float FBy = rB * (-d.g_ads * ady - d.g_coh * cBy);
     // ---- Shan-Chen shift and BGK -----------------------------------------
     const float den = rA * d.inv_tau_a + rB * d.inv_tau_b;
-    const float iden = den > 0.f ? __frcp_rn(den) : 0.f;
+    const float iden = den > 1e-30f ? rcp_nr(den) : 0.f;
     const float upx = (jAx * d.inv_tau_a + jBx * d.inv_tau_b) * iden;
     const float upy = (jAy * d.inv_tau_a + jBy * d.inv_tau_b) * iden;
-    const float sA = rA > 1e-12f ? d.tau_a * __frcp_rn(rA) : 0.f;
-    const float sB = rB > 1e-12f ? d.tau_b * __frcp_rn(rB) : 0.f;
+    const float sA = rA > 1e-12f ? d.tau_a * rcp_nr(rA) : 0.f;
+    const float sB = rB > 1e-12f ? d.tau_b * rcp_nr(rB) : 0.f;
     bgk9(fA, rA, upx + sA * FAx, upy + sA * FAy, d.inv_tau_a);
     bgk9(fB, rB, upx + sB * FBx, upy + sB * FBy, d.inv_tau_b);
     // ---- solute ----------------------------------------------------------
     const float rt = rA + rB;
-    const float irt = rt > 0.f ? __frcp_rn(rt) : 0.f;
+    const float irt = rt > 1e-30f ? rcp_nr(rt) : 0.f;
     const float ux = ((jAx + jBx) + 0.5f * (FAx + FBx)) * irt;
     const float uy = ((jAy + jBy) + 0.5f * (FAy + FBy)) * irt;
     {

@@ -67,7 +67,7 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
-            f[i] = __fmul_rn(wq(i), __fmaf_rn(dv, kInvDevScale, rt));  // see TMA kernel
+            f[i] = dec_pop(i, dv, rt);
         }
     }
 }
@@ -93,7 +93,7 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
         } else {
             const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
             const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
-            g[k] = __fmul_rn(0.25f, __fmaf_rn(dv, kInvDevScale, ct));
+            g[k] = dec_sol(dv, ct);
         }
     }
 }

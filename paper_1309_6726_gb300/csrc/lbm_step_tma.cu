@@ -137,49 +137,107 @@ struct TmaTile {
     static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0, "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(NRING <= NT && NRING / NW < 32, "ring spread");
+    static_assert(TX % 32 == 0, "a warp covers 32 columns of one row");
 };
 
 // The 9 populations of component `comp` pulled into the node at stage cell
-// `c`, from shared memory (bb: bounce-back bits).
-template <class S, class TT>
+// `c`, from shared memory (bb: bounce-back bits).  BB = false: no source is
+// solid, every address is the node's cell plus a constant.
+template <class S, class TT, bool BB>
 __device__ __forceinline__ void spull9(const typename S::T *tile,
                                        const __half *mom, int comp, int c,
                                        unsigned bb, float f[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const bool b = (bb >> i) & 1u;
+        const bool b = BB && ((bb >> i) & 1u);
         const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
         const int q = comp * Q + (b ? opp(i) : i);
         if constexpr (!S::kHalf) {
             f[i] = tile[q * TT::PL + cell];
         } else {
-            // explicit roundings: no fused multiply-add may merge this
-            // product into a later sum, so every pull of a node's
-            // population (own node or density ring) gives the same bits
-            f[i] = __fmul_rn(wq(i), __fmaf_rn(__half2float(tile[q * TT::PL + cell]),
-                                              kInvDevScale,
-                                              __half2float(mom[comp * TT::PL + cell])));
+            f[i] = dec_pop(b ? opp(i) : i, __half2float(tile[q * TT::PL + cell]),
+                           __half2float(mom[comp * TT::PL + cell]));
         }
     }
 }
 
-template <class S, class TT>
+template <class S, class TT, bool BB>
 __device__ __forceinline__ void spull4(const typename S::T *tile,
                                        const __half *mom, int c, unsigned bb4,
                                        float g[QS]) {
 #pragma unroll
     for (int k = 0; k < QS; ++k) {
-        const bool b = (bb4 >> k) & 1u;
+        const bool b = BB && ((bb4 >> k) & 1u);
         const int cell = b ? c : c - sy(k) * TT::BX - sx(k);
         const int q = 2 * Q + (b ? sopp(k) : k);
         if constexpr (!S::kHalf) {
             g[k] = tile[q * TT::PL + cell];
         } else {
-            g[k] = __fmul_rn(0.25f, __fmaf_rn(__half2float(tile[q * TT::PL + cell]),
-                                              kInvDevScale,
-                                              __half2float(mom[2 * TT::PL + cell])));
+            g[k] = dec_sol(__half2float(tile[q * TT::PL + cell]),
+                           __half2float(mom[2 * TT::PL + cell]));
         }
     }
+}
+
+// The 22 populations of the node at stage cell c.
+template <class S, class TT>
+__device__ __forceinline__ void spull22(const typename S::T *tile,
+                                        const __half *mom, int c, unsigned bb,
+                                        float fA[Q], float fB[Q], float g[QS]) {
+    if (bb == 0u) {
+        spull9<S, TT, false>(tile, mom, 0, c, 0u, fA);
+        spull9<S, TT, false>(tile, mom, 1, c, 0u, fB);
+        spull4<S, TT, false>(tile, mom, c, 0u, g);
+    } else {
+        spull9<S, TT, true>(tile, mom, 0, c, bb, fA);
+        spull9<S, TT, true>(tile, mom, 1, c, bb, fB);
+        spull4<S, TT, true>(tile, mom, c, (bb >> 1) & 0xFu, g);
+    }
+}
+
+// Densities of both components at stage cell c.
+template <class S, class TT>
+__device__ __forceinline__ void sdens(const typename S::T *tile,
+                                      const __half *mom, int c, unsigned bb,
+                                      float &ra, float &rb) {
+    float f[Q];
+    ra = 0.f;
+    rb = 0.f;
+    if (bb == 0u) {
+        spull9<S, TT, false>(tile, mom, 0, c, 0u, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ra += f[i];
+        spull9<S, TT, false>(tile, mom, 1, c, 0u, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rb += f[i];
+    } else {
+        spull9<S, TT, true>(tile, mom, 0, c, bb, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ra += f[i];
+        spull9<S, TT, true>(tile, mom, 1, c, bb, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rb += f[i];
+    }
+}
+
+// True when no node in rows ly - 1 .. ly + 1, columns c0 - 1 .. c0 + 32 of
+// the tile (c0 = this warp's first column) has `bits` set in the mask box:
+// then every node of the warp has no solid neighbour and no solid source.
+// The 34 bytes of a row lie in 10 aligned words; lane j < 30 tests one.
+template <class TT>
+__device__ __forceinline__ bool warp_clean(const uint8_t *sm, int ly, int c0,
+                                           int lane, uint8_t bits) {
+    bool dirty = false;
+    if (lane < 30) {
+        const int row = lane / 10, w = lane % 10;
+        const int off = (ly + 1 + row) * TT::MBX + TT::MXO + c0 - 4 + 4 * w;
+        unsigned keep = 0xFFFFFFFFu;
+        if (w == 0) keep = 0xFF000000u;  // column c0 - 1 only
+        if (w == 9) keep = 0x000000FFu;  // column c0 + 32 only
+        const unsigned v = *reinterpret_cast<const unsigned *>(sm + off);
+        dirty = (v & keep & (bits * 0x01010101u)) != 0u;
+    }
+    return !__any_sync(0xFFFFFFFFu, dirty);
 }
 
 // Mask bits around the node at mask-box cell mc: bit i of the result is set
@@ -199,7 +257,7 @@ __global__ void __launch_bounds__(TX *TY)
     k_step_tma(StepArgs a, const CUtensorMap *__restrict__ pop_maps,
                const CUtensorMap *__restrict__ mom_maps,
                const CUtensorMap *__restrict__ mask_maps,
-               const int *__restrict__ sched, int nslots,
+               const TileRec *__restrict__ sched, int nslots,
                int *__restrict__ err) {
     using TT = TmaTile<S, TX, TY>;
     using T = typename S::T;
@@ -218,32 +276,29 @@ __global__ void __launch_bounds__(TX *TY)
     };
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TT::BAR_OFF);
     long long *s_t = reinterpret_cast<long long *>(bar + 2);
-    int *s_tile = reinterpret_cast<int *>(bar + 3);  // tile of each desc slot
+    TileRec *s_rec = reinterpret_cast<TileRec *>(bar + 4);  // tile of each desc slot
 
     // This block's tiles: sched[blockIdx.x + k * gridDim.x], k = 0, 1, ...,
     // until the first -1; consecutive entries walk down one tile column of a
     // lattice, so the halo rows a tile copies were copied by the previous
     // tile of the same block and come from L2.
     auto sched_at = [&](int k) {
-        return k < nslots ? sched[blockIdx.x + (size_t)k * gridDim.x] : -1;
+        return k < nslots ? sched[blockIdx.x + (size_t)k * gridDim.x]
+                          : TileRec{-1, 0, 0, 0};
     };
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const T *__restrict__ fin = static_cast<const T *>(a.fin);
 
-    // Copies tile `tile` into stage s and its lattice descriptor into `slot`.
-    auto issue = [&](int tile, int s, int slot) {
-        const int l = a.tile_lat[tile];
-        const LatDesc *gd = a.desc + l;
-        const int local = tile - gd->tile_base;
-        const int tiles_x = gd->tiles_x;
-        // physical coordinates: column x0 - XO and row ty0 - 2 of the lattice
-        const int x0 = (local % tiles_x) * TX + XGHOST;
-        const int y0 = (local / tiles_x) * TY;
+    // Copies tile r into stage s and its lattice descriptor into `slot`.
+    auto issue = [&](const TileRec &r, int s, int slot) {
+        const int l = r.lat;
+        // physical coordinates: column x0 - XO and row y0 - 2 of the lattice
+        const int x0 = r.x0 + XGHOST;
+        const int y0 = r.y0;
         fence_proxy_async();
         mbar_expect_tx(&bar[s], TT::TX_BYTES);
-        bulk_load(sdesc(slot), gd, 128, &bar[s]);
+        bulk_load(sdesc(slot), a.desc + l, 128, &bar[s]);
         tma_load_3d(stage_pop(s), &pop_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
         if constexpr (S::kHalf)
             tma_load_3d(stage_mom(s), &mom_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
@@ -255,18 +310,24 @@ __global__ void __launch_bounds__(TX *TY)
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         *s_t = *(volatile long long *)a.step;
-        const int t0 = sched_at(0), t1 = t0 >= 0 ? sched_at(1) : -1;
-        s_tile[0] = t0;
-        s_tile[1] = t1;
-        if (t0 >= 0) issue(t0, 0, 0);
-        if (t1 >= 0) issue(t1, 1, 1);
+        const TileRec t0 = sched_at(0);
+        const TileRec t1 = t0.lat >= 0 ? sched_at(1) : TileRec{-1, 0, 0, 0};
+        s_rec[0] = t0;
+        s_rec[1] = t1;
+        s_rec[2] = TileRec{-1, 0, 0, 0};
+        if (t0.lat >= 0) issue(t0, 0, 0);
+        if (t1.lat >= 0) issue(t1, 1, 1);
     }
     __syncthreads();
     const long long t = *s_t;
     const MaskBits mb(t);
 
     unsigned parity = 0u;  // bit s: phase parity of stage s
-    for (int k = 0; s_tile[k % 3] >= 0; ++k) {
+    for (int k = 0; s_rec[k % 3].lat >= 0; ++k) {
+        // the record of the tile after next, fetched now so that its load
+        // latency hides behind this tile's work
+        TileRec nxt{-1, 0, 0, 0};
+        if (tid == 0 && s_rec[(k + 1) % 3].lat >= 0) nxt = sched_at(k + 2);
         const int s = k & 1;
         const int slot = k % 3;
         const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
@@ -274,18 +335,16 @@ __global__ void __launch_bounds__(TX *TY)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(err, 1);
-                if (s_tile[(k + 1) % 3] >= 0)
+                if (s_rec[(k + 1) % 3].lat >= 0)
                     mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
             }
             break;
         }
-        const int tile = s_tile[slot];
+        const TileRec rc = s_rec[slot];
         const LatDesc &d = *sdesc(slot);
-        const int l = d.index;
+        const int l = rc.lat;
         const int nx = d.nx, ny = d.ny;
-        const int local = tile - d.tile_base;
-        const int tx0 = (local % d.tiles_x) * TX;
-        const int ty0 = (local / d.tiles_x) * TY;
+        const int tx0 = rc.x0, ty0 = rc.y0;
         // rows / columns of the tile that hold lattice nodes; frame
         // positions further out are never a node's neighbour
         const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
@@ -302,16 +361,18 @@ __global__ void __launch_bounds__(TX *TY)
         const int mc = (ly + 2) * TT::MBX + lx + TT::MXO;  // mask cell
         const uint8_t s_own = in_frame ? sm[mc] : (uint8_t)0xFF;
         const bool own_pull_fluid = !(s_own & mb.pull);
-        const unsigned bb = nb_bits<TT, -1>(sm, mc, mb.pull);   // sources solid
-        const unsigned snb = nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
+        // warps whose rows and their neighbours hold no solid node skip the
+        // neighbour bits (all zero) and the bounce-back selects
+        const bool clean = warp_clean<TT>(sm, ly, lx & ~31, lane,
+                                          (uint8_t)(mb.pull | mb.force));
+        const unsigned bb = clean ? 0u : nb_bits<TT, -1>(sm, mc, mb.pull);   // sources solid
+        const unsigned snb = clean ? 0u : nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
         float fA[Q], fB[Q], g[QS];
         float *fr = srho(s);
         {
             float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
-                spull9<S, TT>(tp, tm, 0, pc, bb, fA);
-                spull9<S, TT>(tp, tm, 1, pc, bb, fB);
-                spull4<S, TT>(tp, tm, pc, (bb >> 1) & 0xFu, g);
+                spull22<S, TT>(tp, tm, pc, bb, fA, fB, g);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
             }
@@ -333,13 +394,7 @@ __global__ void __launch_bounds__(TX *TY)
                 float ra = 0.f, rb = 0.f;
                 if (!(sm[rmc] & mb.force)) {
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
-                    float f[Q];
-                    spull9<S, TT>(tp, tm, 0, rpc, rbb, f);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) ra += f[i];
-                    spull9<S, TT>(tp, tm, 1, rpc, rbb, f);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) rb += f[i];
+                    sdens<S, TT>(tp, tm, rpc, rbb, ra, rb);
                 }
                 fr[ry * TT::RX + rx] = ra;
                 fr[TT::RX * TT::RY + ry * TT::RX + rx] = rb;
@@ -349,9 +404,8 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         // stage s is free: start the copy of the tile after next into it
         if (tid == 0) {
-            const int t2 = s_tile[(k + 1) % 3] >= 0 ? sched_at(k + 2) : -1;
-            s_tile[(k + 2) % 3] = t2;
-            if (t2 >= 0) issue(t2, s, (k + 2) % 3);
+            s_rec[(k + 2) % 3] = nxt;
+            if (nxt.lat >= 0) issue(nxt, s, (k + 2) % 3);
         }
 
         if (active) {
@@ -401,7 +455,7 @@ static cudaError_t grid_tma_t(int *grid) {
 template <class S, int TX, int TY>
 static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
                                 const CUtensorMap *mom_maps,
-                                const CUtensorMap *mask_maps, const int *sched,
+                                const CUtensorMap *mask_maps, const TileRec *sched,
                                 int nslots, int grid, int *err, cudaStream_t s) {
     using TT = TmaTile<S, TX, TY>;
     k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(
@@ -425,7 +479,7 @@ cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
-                            const CUtensorMap *mask_maps, const int *sched,
+                            const CUtensorMap *mask_maps, const TileRec *sched,
                             int nslots, int grid, int tx, int ty, bool half,
                             int *err, cudaStream_t s) {
 #define LBM_TMA_CASE(X, Y)                                                   \
