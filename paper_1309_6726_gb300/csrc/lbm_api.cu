@@ -22,9 +22,11 @@ cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
                                int ty, bool half, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
-                            const CUtensorMap *mask_maps, const TileRec *sched,
-                            int nslots, int grid, int tx, int ty, bool half,
-                            int *err, cudaStream_t s);
+                            const CUtensorMap *mask_maps,
+                            const CUtensorMap *out_maps,
+                            const CUtensorMap *out_mom_maps,
+                            const TileRec *sched, int nslots, int grid, int tx,
+                            int ty, bool half, int *err, cudaStream_t s);
 cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
 int tma_box_x(int tx, bool half);
 int tma_mask_box_x(int tx);
@@ -84,8 +86,11 @@ struct lbm_handle {
     float *d_canon = nullptr;      // [22][ny][nx] scratch of one lattice
     float *d_dens = nullptr;       // [3][ny][nx]
     double *d_dep = nullptr;       // [ny][nx]
-    CUtensorMap *d_maps = nullptr;     // [2 buffers][count] population maps
-    CUtensorMap *d_mom_maps = nullptr; // [2 buffers][count] FP16 moment maps
+    // [2 buffers][count] population (FP16 moment) maps over the ghost band
+    // for the tile copies, then [2 buffers][count] over the lattice itself
+    // for the output stores
+    CUtensorMap *d_maps = nullptr;
+    CUtensorMap *d_mom_maps = nullptr;
     CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
     TileRec *d_sched = nullptr;        // TMA kernel: tiles of each block
     int sched_grid = 0, sched_slots = 0;
@@ -198,7 +203,9 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     }
     const int count = h->count;
     const size_t esz = h->half ? 2 : 4;
-    std::vector<CUtensorMap> maps(2 * count), moms(2 * count);
+    std::vector<CUtensorMap> maps(4 * count), moms(4 * count);
+    const CUtensorMapDataType pty =
+        h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int b = 0; b < 2; ++b) {
         for (int l = 0; l < count; ++l) {
             const LatDesc &d = h->desc[l];
@@ -210,10 +217,7 @@ static bool make_maps(lbm_handle *h, std::string &why) {
             cuuint32_t es[3] = {1, 1, 1};
             void *base = (char *)h->d_pop[b] +
                          (size_t)(d.pop_off - GHOST * d.pitch - XGHOST) * esz;
-            CUresult r = enc(&maps[b * count + l],
-                             h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                             3, base, dims, strides, box, es,
+            CUresult r = enc(&maps[b * count + l], pty, 3, base, dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE,
                              CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -235,6 +239,33 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
                 if (r != CUDA_SUCCESS) {
                     why = "cuTensorMapEncodeTiled failed for moments, code " +
+                          std::to_string((int)r);
+                    return false;
+                }
+            }
+            // output: the lattice's own nodes, logical (0, 0) at the base
+            // (16-byte aligned: the ghost band is 16 columns wide)
+            cuuint64_t odims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NPOP};
+            cuuint32_t obox[3] = {(cuuint32_t)h->tx, (cuuint32_t)h->ty, (cuuint32_t)NPOP};
+            r = enc(&maps[(2 + b) * count + l], pty, 3,
+                    (char *)h->d_pop[b] + (size_t)d.pop_off * esz, odims, strides,
+                    obox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                why = "cuTensorMapEncodeTiled failed for the output, code " +
+                      std::to_string((int)r);
+                return false;
+            }
+            if (h->half) {
+                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NMOM};
+                cuuint32_t mbox[3] = {obox[0], obox[1], (cuuint32_t)NMOM};
+                r = enc(&moms[(2 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                        (char *)h->d_mom[b] + (size_t)d.mom_off * 2, mdims, strides,
+                        mbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    why = "cuTensorMapEncodeTiled failed for the moment output, code " +
                           std::to_string((int)r);
                     return false;
                 }
@@ -648,14 +679,22 @@ static StepArgs step_args(lbm_handle *h) {
     return a;
 }
 
+// One launch of the TMA step kernel reading buffer cur, writing cur ^ 1.
+static cudaError_t launch_tma(lbm_handle *h) {
+    const int c = h->count, in = h->cur, out = h->cur ^ 1;
+    return launch_step_tma(
+        step_args(h), h->d_maps + in * c,
+        h->half ? h->d_mom_maps + in * c : nullptr, h->d_mask_maps,
+        h->d_maps + (2 + out) * c,
+        h->half ? h->d_mom_maps + (2 + out) * c : nullptr, h->d_sched,
+        h->sched_slots, h->sched_grid, h->tx, h->ty, h->half, h->d_err,
+        h->stream);
+}
+
 static cudaError_t launch_one(lbm_handle *h) {
     StepArgs a = step_args(h);
     return h->use_tma
-               ? launch_step_tma(a, h->d_maps + h->cur * h->count,
-                                 h->half ? h->d_mom_maps + h->cur * h->count : nullptr,
-                                 h->d_mask_maps, h->d_sched, h->sched_slots,
-                                 h->sched_grid, h->tx, h->ty, h->half, h->d_err,
-                                 h->stream)
+               ? launch_tma(h)
                : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
 }
 
@@ -708,11 +747,7 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
         StepArgs a = step_args(h);
         cudaError_t e =
             h->use_tma
-                ? launch_step_tma(a, h->d_maps + h->cur * h->count,
-                                  h->half ? h->d_mom_maps + h->cur * h->count : nullptr,
-                                  h->d_mask_maps, h->d_sched, h->sched_slots,
-                                  h->sched_grid, h->tx, h->ty, h->half, h->d_err,
-                                  h->stream)
+                ? launch_tma(h)
                 : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
         if (e == cudaErrorInvalidValue && k == 0)
             return fail(h, LBM_EINVAL, "unsupported tile shape");

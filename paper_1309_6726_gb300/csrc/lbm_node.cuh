@@ -128,16 +128,30 @@ __device__ __forceinline__ void store_node22(const StepArgs &a,
     store4<S>(p + 2 * Q * pl, S::kHalf ? mp + 2 * pl : nullptr, pl, g);
 }
 
+// Writes the 22 post-collision values of the tile node at `o` (planes NT
+// apart) -- a shared-memory tile that a bulk tensor store then copies out.
+template <class S, int NT>
+__device__ __forceinline__ void store_tile22(typename S::T *o, __half *om,
+                                             const float fA[Q],
+                                             const float fB[Q],
+                                             const float g[QS]) {
+    store9<S>(o, om, NT, fA);
+    store9<S>(o + Q * NT, S::kHalf ? om + NT : nullptr, NT, fB);
+    store4<S>(o + 2 * Q * NT, S::kHalf ? om + 2 * NT : nullptr, NT, g);
+}
+
 // Everything after the pull, for a node that is fluid in s_t.
 //   fA, fB, g: post-streaming populations of the node (g pulled already);
 //   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
 //   snb: bit i set if x + e_i is solid in s_t;  ns: solid D2Q4 links.
+// put(fA, fB, g) writes the node's own post-collision values; its periodic
+// images in the ghost band are written here.
 // Returns true if the node reached the threshold in this step.
-template <class S>
+template <class S, class Put>
 __device__ __forceinline__ bool fluid_update(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
     int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
-    const float rhoB_nb[Q], unsigned snb, int ns) {
+    const float rhoB_nb[Q], unsigned snb, int ns, Put put) {
     using T = typename S::T;
     // ---- moments ----------------------------------------------------------
     float rA, jAx, jAy, rB, jBx, jBy;
@@ -204,7 +218,7 @@ __device__ __forceinline__ bool fluid_update(
         }
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
-    store_node22<S>(a, d, own, fA, fB, g);
+    put(fA, fB, g);
     // periodic images in the ghost band
     for_ghosts(gx, gy, d.nx, d.ny, d.pitch, own,
                [&](int off) { store_node22<S>(a, d, off, fA, fB, g); });

@@ -205,8 +205,11 @@ __global__ void __launch_bounds__(TX *TY)
                 if (smask[hy + cy(i)][hx + cx(i)] & mb.force) snb |= 1u << i;
             }
             pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
-            const bool flagged = fluid_update<S>(a, d, l, t, gx, gy, own, fA, fB, g,
-                                                 rAn, rBn, snb, ns);
+            const bool flagged = fluid_update<S>(
+                a, d, l, t, gx, gy, own, fA, fB, g, rAn, rBn, snb, ns,
+                [&](const float *pa, const float *pb, const float *pg) {
+                    store_node22<S>(a, d, own, pa, pb, pg);
+                });
             if (flagged) mask_store(mask, own, gx, gy, nx, ny, d.pitch, s_own | mb.next);
         }
     }

@@ -10,8 +10,8 @@
 //     the x start stays 16-byte aligned -- into shared memory, completing
 //     on an mbarrier; FP16 storage adds a second copy of the 3 moment
 //     planes;
-//   * two stages: the copy of the next tile is in flight while the current
-//     one is computed;
+//   * three stages where they fit in shared memory (else two): the copies
+//     of the next tiles are in flight while the current one is computed;
 //   * all pulls -- the tile's own nodes and the one-node density ring the
 //     cohesion stencil needs -- then read shared memory at fixed offsets;
 //   * the lattice planes carry a two-node periodic ghost band (rows and
@@ -97,6 +97,29 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
         : "memory");
 }
 
+// Bulk tensor store of a shared-memory box to global memory (elements
+// outside the tensor are skipped), committed as one bulk group.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map,
+                                             const void *src, int c0, int c1,
+                                             int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group "
+        "[%0, {%1, %2, %3}], [%4];" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// The shared memory of every committed store has been read.
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Every committed store has completed.
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void *dst, const void *src,
                                           unsigned bytes, uint64_t *bar) {
     asm volatile(
@@ -130,10 +153,26 @@ struct TmaTile {
     static constexpr int RX = TX + 2, RY = TY + 2;  // density frame
     static constexpr int NRING = 2 * RX + 2 * TY;
     static constexpr int RHO_BYTES = 2 * RX * RY * 4;
-    static constexpr int DESC_OFF = 2 * STAGE;                 // 3 x 128
-    static constexpr int RHO_OFF = DESC_OFF + 3 * 128;         // 2 frames
-    static constexpr int BAR_OFF = RHO_OFF + 2 * ((RHO_BYTES + 127) / 128 * 128);
+    static constexpr int RHO_AL = (RHO_BYTES + 127) / 128 * 128;
+    // Two stages: the copy of the next tile lands while this one is
+    // computed (a third stage measured no faster).  One descriptor slot
+    // more than stages: the current tile's stays readable while the next
+    // copies land.
+    static constexpr int NS = 2;
+    static constexpr int NSL = NS + 1;
+    static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
+    static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
+    // The tile's post-collision output, [22][TY][TX] (+ [3][TY][TX] FP16
+    // references), written by bulk tensor stores -- where it fits.
+    static constexpr int OUT_POP = NPOP * NT * (int)sizeof(T);
+    static constexpr int OUT_BYTES =
+        (OUT_POP + (S::kHalf ? NMOM * NT * 2 : 0) + 127) / 128 * 128;
+    static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
+    static constexpr bool TS = OUT_OFF + OUT_BYTES + 128 <= 232448;
+    static constexpr int BAR_OFF = OUT_OFF + (TS ? OUT_BYTES : 0);
     static constexpr int SMEM = BAR_OFF + 128;
+    static_assert(SMEM <= 232448, "shared memory per block");
+    static_assert((TX * (int)sizeof(T)) % 16 == 0, "store box row");
     static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0, "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(NRING <= NT && NRING / NW < 32, "ring spread");
@@ -257,6 +296,8 @@ __global__ void __launch_bounds__(TX *TY)
     k_step_tma(StepArgs a, const CUtensorMap *__restrict__ pop_maps,
                const CUtensorMap *__restrict__ mom_maps,
                const CUtensorMap *__restrict__ mask_maps,
+               const CUtensorMap *__restrict__ out_maps,
+               const CUtensorMap *__restrict__ out_mom_maps,
                const TileRec *__restrict__ sched, int nslots,
                int *__restrict__ err) {
     using TT = TmaTile<S, TX, TY>;
@@ -270,12 +311,12 @@ __global__ void __launch_bounds__(TX *TY)
     auto sdesc = [&](int slot) {
         return reinterpret_cast<LatDesc *>(smem + TT::DESC_OFF + 128 * slot);
     };
-    auto srho = [&](int s) {
-        return reinterpret_cast<float *>(smem + TT::RHO_OFF +
-                                         s * ((TT::RHO_BYTES + 127) / 128 * 128));
+    auto srho = [&](int f) {
+        return reinterpret_cast<float *>(smem + TT::RHO_OFF + f * TT::RHO_AL);
     };
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TT::BAR_OFF);
-    long long *s_t = reinterpret_cast<long long *>(bar + 2);
+    constexpr int NS = TT::NS, NSL = TT::NSL;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TT::BAR_OFF);  // NS
+    long long *s_t = reinterpret_cast<long long *>(bar + 3);
     TileRec *s_rec = reinterpret_cast<TileRec *>(bar + 4);  // tile of each desc slot
 
     // This block's tiles: sched[blockIdx.x + k * gridDim.x], k = 0, 1, ...,
@@ -306,39 +347,62 @@ __global__ void __launch_bounds__(TX *TY)
     };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int j = 0; j < NS; ++j) mbar_init(&bar[j], 1);
         fence_mbar_init();
         *s_t = *(volatile long long *)a.step;
-        const TileRec t0 = sched_at(0);
-        const TileRec t1 = t0.lat >= 0 ? sched_at(1) : TileRec{-1, 0, 0, 0};
-        s_rec[0] = t0;
-        s_rec[1] = t1;
-        s_rec[2] = TileRec{-1, 0, 0, 0};
-        if (t0.lat >= 0) issue(t0, 0, 0);
-        if (t1.lat >= 0) issue(t1, 1, 1);
+        bool more = true;
+        for (int j = 0; j < NSL; ++j) {
+            const TileRec r = more && j < NS ? sched_at(j) : TileRec{-1, 0, 0, 0};
+            s_rec[j] = r;
+            more = r.lat >= 0;
+            if (more) issue(r, j, j);
+        }
     }
     __syncthreads();
     const long long t = *s_t;
     const MaskBits mb(t);
 
+    // output tile in shared memory (TS): node lid = ly * TX + lx of plane q
+    // at sout[q * NT + lid]; FP16 references at smom_out[c * NT + lid]
+    T *sout = reinterpret_cast<T *>(smem + TT::OUT_OFF);
+    __half *smom_out = reinterpret_cast<__half *>(smem + TT::OUT_OFF + TT::OUT_POP);
+    // bulk tensor store of the output tile (thread 0; every thread fenced
+    // its writes and passed a barrier since)
+    auto store_out = [&](const TileRec &r) {
+        tma_store_3d(&out_maps[r.lat], sout, r.x0, r.y0, 0);
+        if constexpr (S::kHalf)
+            tma_store_3d(&out_mom_maps[r.lat], smom_out, r.x0, r.y0, 0);
+        bulk_commit();
+    };
+    TileRec prev{-1, 0, 0, 0};  // thread 0: the tile whose output awaits its store
+    bool failed = false;
+
     unsigned parity = 0u;  // bit s: phase parity of stage s
-    for (int k = 0; s_rec[k % 3].lat >= 0; ++k) {
-        // the record of the tile after next, fetched now so that its load
+    for (int k = 0; s_rec[k % NSL].lat >= 0; ++k) {
+        // the record of the tile NS ahead, fetched now so that its load
         // latency hides behind this tile's work
         TileRec nxt{-1, 0, 0, 0};
-        if (tid == 0 && s_rec[(k + 1) % 3].lat >= 0) nxt = sched_at(k + 2);
-        const int s = k & 1;
-        const int slot = k % 3;
+        if (tid == 0 && s_rec[(k + NS - 1) % NSL].lat >= 0) nxt = sched_at(k + NS);
+        const int s = k % NS;
+        const int slot = k % NSL;
         const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
         parity ^= 1u << s;
         if (__syncthreads_or(!ok)) {
+            // give up: let the copies still in flight land before exiting
             if (tid == 0) {
                 atomicOr(err, 1);
-                if (s_rec[(k + 1) % 3].lat >= 0)
-                    mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
+                for (int j = 1; j < NS; ++j) {
+                    if (s_rec[(k + j) % NSL].lat < 0) break;
+                    const int sj = (k + j) % NS;
+                    mbar_wait_bounded(&bar[sj], (parity >> sj) & 1u);
+                }
             }
+            failed = true;
             break;
+        }
+        if constexpr (TT::TS) {
+            // every thread finished the previous tile's output
+            if (tid == 0 && prev.lat >= 0) store_out(prev);
         }
         const TileRec rc = s_rec[slot];
         const LatDesc &d = *sdesc(slot);
@@ -368,7 +432,7 @@ __global__ void __launch_bounds__(TX *TY)
         const unsigned bb = clean ? 0u : nb_bits<TT, -1>(sm, mc, mb.pull);   // sources solid
         const unsigned snb = clean ? 0u : nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
         float fA[Q], fB[Q], g[QS];
-        float *fr = srho(s);
+        float *fr = srho(k & 1);
         {
             float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
@@ -401,11 +465,25 @@ __global__ void __launch_bounds__(TX *TY)
             }
         }
         fence_proxy_async();
+        // Output through shared memory and a bulk tensor store, except for
+        // tiles that end past the lattice's last column: a store box that
+        // crosses x = nx was measured to overwrite the ghost columns there
+        // (partial 16-byte rows are not clipped element by element), so
+        // those tiles store their nodes directly.
+        const bool ts_tile = TT::TS && tx0 + TX <= nx;
+        if constexpr (TT::TS) {
+            // the output tile is rewritten below: its last store must have
+            // read it
+            if (tid == 0) {
+                bulk_wait_read();
+                prev = ts_tile ? rc : TileRec{-1, 0, 0, 0};
+            }
+        }
         __syncthreads();
-        // stage s is free: start the copy of the tile after next into it
+        // stage s is free: start the copy of the tile NS ahead into it
         if (tid == 0) {
-            s_rec[(k + 2) % 3] = nxt;
-            if (nxt.lat >= 0) issue(nxt, s, (k + 2) % 3);
+            s_rec[(k + NS) % NSL] = nxt;
+            if (nxt.lat >= 0) issue(nxt, s, (k + NS) % NSL);
         }
 
         if (active) {
@@ -423,11 +501,26 @@ __global__ void __launch_bounds__(TX *TY)
                     rBn[i] = fr[TT::RX * TT::RY + fc];
                 }
                 const int ns = __popc(snb & 0x1Eu);
-                const bool flagged = fluid_update<S>(a, d, l, t, x, y, own, fA, fB, g,
-                                                     rAn, rBn, snb, ns);
+                const int lid = ly * TX + lx;
+                const bool flagged = fluid_update<S>(
+                    a, d, l, t, x, y, own, fA, fB, g, rAn, rBn, snb, ns,
+                    [&](const float *pa, const float *pb, const float *pg) {
+                        if (ts_tile)
+                            store_tile22<S, TT::NT>(sout + lid, smom_out + lid, pa, pb, pg);
+                        else
+                            store_node22<S>(a, d, own, pa, pb, pg);
+                    });
                 if (flagged)
                     mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, s_own | mb.next);
             }
+        }
+        if constexpr (TT::TS) fence_proxy_async();  // before the next barrier
+    }
+    if constexpr (TT::TS) {
+        __syncthreads();
+        if (tid == 0) {
+            if (!failed && prev.lat >= 0) store_out(prev);
+            bulk_wait_all();
         }
     }
     finish_launch(a, t);
@@ -455,11 +548,15 @@ static cudaError_t grid_tma_t(int *grid) {
 template <class S, int TX, int TY>
 static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
                                 const CUtensorMap *mom_maps,
-                                const CUtensorMap *mask_maps, const TileRec *sched,
-                                int nslots, int grid, int *err, cudaStream_t s) {
+                                const CUtensorMap *mask_maps,
+                                const CUtensorMap *out_maps,
+                                const CUtensorMap *out_mom_maps,
+                                const TileRec *sched, int nslots, int grid,
+                                int *err, cudaStream_t s) {
     using TT = TmaTile<S, TX, TY>;
     k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(
-        a, pop_maps, mom_maps, mask_maps, sched, nslots, err);
+        a, pop_maps, mom_maps, mask_maps, out_maps, out_mom_maps, sched,
+        nslots, err);
     return cudaGetLastError();
 }
 
@@ -479,24 +576,29 @@ cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
-                            const CUtensorMap *mask_maps, const TileRec *sched,
-                            int nslots, int grid, int tx, int ty, bool half,
-                            int *err, cudaStream_t s) {
+                            const CUtensorMap *mask_maps,
+                            const CUtensorMap *out_maps,
+                            const CUtensorMap *out_mom_maps,
+                            const TileRec *sched, int nslots, int grid, int tx,
+                            int ty, bool half, int *err, cudaStream_t s) {
 #define LBM_TMA_CASE(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
         return half ? launch_tma_t<Store16, X, Y>(a, pop_maps, mom_maps,     \
-                                                  mask_maps, sched, nslots,  \
-                                                  grid, err, s)              \
+                                                  mask_maps, out_maps,       \
+                                                  out_mom_maps, sched,       \
+                                                  nslots, grid, err, s)      \
                     : launch_tma_t<Store32, X, Y>(a, pop_maps, mom_maps,     \
-                                                  mask_maps, sched, nslots,  \
-                                                  grid, err, s);
+                                                  mask_maps, out_maps,       \
+                                                  out_mom_maps, sched,       \
+                                                  nslots, grid, err, s);
     LBM_TMA_SHAPES(LBM_TMA_CASE)
 #undef LBM_TMA_CASE
     return cudaErrorInvalidValue;
 }
 
 // Tensor map geometry must match TmaTile: box (TX + 2 XO) x (TY + 4) x
-// planes for populations and moments, (TX + 32) x (TY + 4) for the mask.
+// planes for populations and moments, (TX + 32) x (TY + 4) for the mask;
+// the output maps span the lattice itself with box TX x TY x planes.
 int tma_box_x(int tx, bool half) { return tx + 2 * (half ? 8 : 4); }
 int tma_mask_box_x(int tx) { return tx + 32; }
 
