@@ -10,24 +10,24 @@
  * The time step it runs is the paper's Sec. II model, per node and step:
  *
  *   streaming of the two D2Q9 populations and the D2Q4 solute with
- *   half-way bounce-back at the solid ("bounce-back rule", Sec. II);
+ *   half-way bounce-back at the solid (the wall rule of Sec. II);
  *   densities and momenta;
  *   Martys-Chen cohesive (A-B) and adhesive (fluid-solid) forces,
  *     F_s = -G_c rho_s(x) sum_i w_i rho_s'(x+e_i) e_i
  *           - G_ads,s rho_s(x) sum_i w_i solid(x+e_i) e_i,
- *     G_ads,A = -g_ads, G_ads,B = +g_ads ("cohesive ... adhesive forces",
+ *     G_ads,A = -g_ads, G_ads,B = +g_ads (the two interaction forces of
  *     Sec. II; g_ads sets the 30 degree contact angle of Sec. I);
  *   Shan-Chen velocity shift and BGK collision of each component;
  *   BGK collision of the D2Q4 solute advected by the barycentric velocity
- *     ("weak coupling with fluid flow", Sec. II), with the inlet column
+ *     (the solute is carried by the flow without acting on it, Sec. II),
+ *     with the inlet column
  *     x = 0 imposing concentration c_in when enabled;
  *   first-order surface reaction k_r at fluid nodes where A is the
  *     majority and that touch the solid: the consumed solute precipitates
- *     ("mass deposits on the surface", Sec. II);
+ *     on the solid surface (Sec. II);
  *   growth: a node whose precipitated mass reaches m_threshold turns solid
- *     ("when the cumulated mass exceeds a threshold value, the solid phase
- *     expands", Sec. II); its fluid, solute and deposit go to a per-lattice
- *     ledger so that mass is accounted exactly.
+ *     (the threshold rule of Sec. II); its fluid, solute and deposit go to
+ *     a per-lattice ledger so that mass is accounted exactly.
  * Lattices are periodic in x and y; node (x, y) is row y, column x.
  *
  * Threading and streams: a handle is not thread-safe.  Calls that only

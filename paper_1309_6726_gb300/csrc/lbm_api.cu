@@ -165,6 +165,12 @@ static bool valid_params(const lbm_params &p, std::string &why) {
 }
 
 static void pick_tile(lbm_handle *h) {
+    // measured defaults on the batched sweep: 32 x 16 for FP32 storage,
+    // 64 x 8 for FP16 (lbm_autotune picks per workload)
+    if (h->half) {
+        h->tx = 64;
+        h->ty = 8;
+    }
     const char *e = getenv("LBM_TILE");
     if (e) {
         int a = 0, b = 0;

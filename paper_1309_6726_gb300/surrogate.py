@@ -1,0 +1,308 @@
+"""A learned surrogate of the batched reactive solver (not part of the paper).
+
+The network of lbm_mlp.h maps the four parameters of one capillary run --
+width W, reaction rate k_r, adhesion strength g_ads, viscosity ratio
+tau_A / tau_B -- to its infiltration curve, the front position z at 64
+log-spaced times, and to its pore-closure time.  It is trained on
+trajectories that the batched lattice Boltzmann solver generates (all
+members of a training set advance together in one persistent launch per
+step), and the solver stays the judge of its error on held-out parameters
+and the fallback for parameters outside the training domain.
+
+Capillary length, reservoirs and the horizon are fixed for a surrogate
+(the inputs exclude them): by default L = 1024 with the sweep's 64-column
+A reservoir and 32-column outlet band, a horizon of 20000 steps, and
+parameters drawn as in the batched sweep (W uniform over 16-128, k_r
+log-uniform on [1e-5, 1e-2], contact angle uniform on [20, 60] degrees
+mapped to g_ads by the calibrated table, tau_A / tau_B uniform on
+[0.6, 1.5]).
+
+    python -m paper_1309_6726_gb300.surrogate [--train 4096] [--held-out 256]
+        [--length 1024] [--steps 20000] [--fit-steps 20000]
+
+prints one JSON line with the dataset cost, the fit and the judged errors.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs as I
+
+N_TIMES = 64
+T_FIRST = 100
+Z_SCALE = 100.0  # lattice units per unit of the front targets
+
+W_RANGE = (16, 128)
+K_RANGE = (1e-5, 1e-2)
+THETA_RANGE = (20.0, 60.0)
+RATIO_RANGE = (0.6, 1.5)
+
+
+def time_grid(t_max: int, n: int = N_TIMES, t_first: int = T_FIRST) -> np.ndarray:
+    """n strictly increasing integer steps, log-spaced from t_first to t_max."""
+    t = np.unique(np.round(np.geomspace(t_first, t_max, n)).astype(np.int64))
+    while t.size < n:  # rounding merged neighbours: fill from the top
+        t = np.unique(np.concatenate([t, [t.max() + 1]]))
+    return t[:n]
+
+
+def draw_members(count: int, seed: int, length: int = 1024):
+    """Run parameters drawn as in the batched sweep, capillary length fixed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        w = int(rng.integers(W_RANGE[0], W_RANGE[1] + 1))
+        k = float(10 ** rng.uniform(math.log10(K_RANGE[0]), math.log10(K_RANGE[1])))
+        th = float(rng.uniform(*THETA_RANGE))
+        tr = float(rng.uniform(*RATIO_RANGE))
+        out.append(I.SweepMember(w, length, k, th, tr))
+    return out
+
+
+def _g_range():
+    # g_ads decreases as the contact angle grows
+    a, b = I.g_ads_for_angle(THETA_RANGE[1]), I.g_ads_for_angle(THETA_RANGE[0])
+    return min(a, b), max(a, b)
+
+
+def features(members) -> np.ndarray:
+    """Network inputs in [-1, 1]: W, log10 k_r, g_ads, tau ratio."""
+    g0, g1 = _g_range()
+    lk0, lk1 = math.log10(K_RANGE[0]), math.log10(K_RANGE[1])
+    rows = []
+    for m in members:
+        g = I.g_ads_for_angle(m.theta_deg)
+        rows.append([
+            2 * (m.width - W_RANGE[0]) / (W_RANGE[1] - W_RANGE[0]) - 1,
+            2 * (math.log10(m.k_r) - lk0) / (lk1 - lk0) - 1,
+            2 * (g - g0) / (g1 - g0) - 1,
+            2 * (m.tau_ratio - RATIO_RANGE[0]) / (RATIO_RANGE[1] - RATIO_RANGE[0]) - 1,
+        ])
+    return np.asarray(rows, np.float32)
+
+
+def in_domain(members, length: int) -> np.ndarray:
+    """True where a run's parameters lie inside the training domain."""
+    f = features(members)
+    ok = np.all(np.abs(f) <= 1.0 + 1e-6, axis=1)
+    return ok & np.array([m.length == length for m in members])
+
+
+def run_trajectories(members, t_grid, precision: str = "fp32"):
+    """Advances all members together on the GPU and records the front
+    position at each time of t_grid and the closure step (-1: none)."""
+    import torch
+    from . import lbm
+    pairs = [I.sweep_lattice(m) for m in members]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = lbm.Solver([g for g, _ in pairs], [p for _, p in pairs], precision)
+    z = np.full((len(members), len(t_grid)), np.nan)
+    done = 0
+    for j, t in enumerate(t_grid):
+        s.step(int(t) - done)
+        done = int(t)
+        obs = s.observables(allow_nan=True)
+        z[:, j] = [o["front"] for o in obs]
+    closure = np.array([o["closure_step"] for o in obs], np.int64)
+    bad = np.array([bool(o["nonfinite"]) for o in obs])
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    nodes = sum(int((g.solid == 0).sum()) for g, _ in pairs)
+    s.close()
+    z[bad] = np.nan
+    return {"z": z, "closure": closure, "nonfinite": bad, "seconds": seconds,
+            "fluid_nodes": nodes, "steps": int(t_grid[-1])}
+
+
+def _log_tmax(t_max):
+    return math.log10(t_max)
+
+
+def targets(z, closure, t_max) -> np.ndarray:
+    """Network targets: z / Z_SCALE at each time, then the closure time as
+    log10(t) / log10(t_max), or (log10(t_max) + 0.3) / log10(t_max) when
+    the run did not close within t_max.  NaN marks what is unknown."""
+    lt = _log_tmax(t_max)
+    c = np.where(closure > 0, np.log10(np.maximum(closure, 1)) / lt,
+                 (lt + 0.3) / lt)
+    y = np.concatenate([z / Z_SCALE, c[:, None]], axis=1).astype(np.float32)
+    bad = np.all(np.isnan(z), axis=1)
+    y[bad, -1] = np.nan
+    return y
+
+
+def decode(y, t_max):
+    """(front [n, times] in lattice units, closure step or -1)."""
+    lt = _log_tmax(t_max)
+    z = y[:, :-1].astype(np.float64) * Z_SCALE
+    lc = y[:, -1].astype(np.float64) * lt
+    closure = np.where(lc < lt + 0.15, np.round(10 ** np.minimum(lc, lt)), -1)
+    return z, closure.astype(np.int64)
+
+
+def judge(z_pred, c_pred, z_lb, c_lb, t_max):
+    """Errors of the surrogate against the solver on the same runs.
+
+    Front: per run, the mean over the times of |z_pred - z_lb| divided by
+    the solver's last front position (at least 10 lattice units).
+    Closure: the relative error of the closure time where both close, and
+    the share of runs where they agree on closing within t_max at all."""
+    ok = ~np.all(np.isnan(z_lb), axis=1)
+    scale = np.maximum(np.nan_to_num(z_lb[:, -1]), 10.0)
+    err = np.array([np.nanmean(np.abs(z_pred[i] - z_lb[i])) / scale[i]
+                    for i in np.flatnonzero(ok)])
+    both = (c_pred > 0) & (c_lb > 0) & ok
+    cerr = np.abs(c_pred[both] / c_lb[both] - 1.0)
+    agree = np.mean((c_pred[ok] > 0) == (c_lb[ok] > 0)) if ok.any() else float("nan")
+    q = lambda a, p: float(np.percentile(a, p)) if a.size else None
+    return {
+        "runs": int(ok.sum()),
+        "front_rel_err_mean": float(err.mean()) if err.size else None,
+        "front_rel_err_median": q(err, 50),
+        "front_rel_err_p90": q(err, 90),
+        "front_within_2pct": float(np.mean(err <= 0.02)) if err.size else None,
+        "closure_runs_both": int(both.sum()),
+        "closure_rel_err_mean": float(cerr.mean()) if cerr.size else None,
+        "closure_rel_err_median": q(cerr, 50),
+        "closure_within_2pct": float(np.mean(cerr <= 0.02)) if cerr.size else None,
+        "closure_agreement": float(agree),
+    }
+
+
+@dataclass
+class FitLog:
+    steps: int
+    seconds: float
+    first_loss: float
+    last_loss: float
+
+
+class Surrogate:
+    """The network (4 inputs, 3 x 256 tanh, 65 outputs) on the GPU."""
+
+    def __init__(self, hidden: int = 256, layers: int = 3, seed: int = 0,
+                 max_batch: int = 8192):
+        from . import mlp
+        self.net = mlp.Mlp(4, hidden, layers, N_TIMES + 1, max_batch)
+        rng = np.random.default_rng(seed)
+        ws, bs = [], []
+        for r, c in mlp.layer_shapes(4, hidden, layers, N_TIMES + 1):
+            lim = math.sqrt(6.0 / (r + c))  # Glorot uniform
+            ws.append(rng.uniform(-lim, lim, (r, c)))
+            bs.append(np.zeros(r))
+        self.net.set_params(mlp.pack(ws, bs))
+
+    def fit(self, x, y, steps: int = 20000, batch: int = 512,
+            lr: float = 2e-3, lr_end: float = 1e-5, seed: int = 0) -> FitLog:
+        """Adam on minibatches with a cosine learning-rate decay."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+        yd = torch.from_numpy(np.ascontiguousarray(y, np.float32)).to(dev)
+        n = xd.shape[0]
+        batch = min(batch, n)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        first = self.net.train_step(xd[:batch].contiguous(), yd[:batch].contiguous(),
+                                    lr, want_loss=True)
+        order = torch.randperm(n, generator=g).to(dev)
+        pos = 0
+        for k in range(1, steps):
+            if pos + batch > n:
+                order = torch.randperm(n, generator=g).to(dev)
+                pos = 0
+            idx = order[pos:pos + batch]
+            pos += batch
+            a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * k / steps))
+            self.net.train_step(xd.index_select(0, idx), yd.index_select(0, idx), a)
+        last = self.net.grad(xd, yd)[1] if n <= self.net.max_batch else float("nan")
+        torch.cuda.synchronize()
+        return FitLog(steps, time.perf_counter() - t0, first, last)
+
+    def predict(self, x) -> np.ndarray:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+        return self.net.forward(xd).cpu().numpy()
+
+    def close(self):
+        self.net.close()
+
+
+def predict_or_solve(model: Surrogate, members, t_grid, length: int):
+    """Answers from the network inside the training domain and from the
+    solver (the fallback) outside it; returns (front, closure, source)."""
+    t_max = int(t_grid[-1])
+    inside = in_domain(members, length)
+    z = np.full((len(members), len(t_grid)), np.nan)
+    c = np.full(len(members), -1, np.int64)
+    if inside.any():
+        zi, ci = decode(model.predict(features([m for m, o in zip(members, inside) if o])), t_max)
+        z[inside], c[inside] = zi, ci
+    if (~inside).any():
+        r = run_trajectories([m for m, o in zip(members, inside) if not o], t_grid)
+        z[~inside], c[~inside] = r["z"], r["closure"]
+    return z, c, np.where(inside, "network", "solver")
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=4096)
+    ap.add_argument("--held-out", type=int, default=256)
+    ap.add_argument("--length", type=int, default=1024)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--fit-steps", type=int, default=20000)
+    ap.add_argument("--seed", type=int, default=1240)
+    ap.add_argument("--save", default=None, help="write the weights (.npy)")
+    args = ap.parse_args(argv)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    grid = time_grid(args.steps)
+    train_m = draw_members(args.train, args.seed, args.length)
+    test_m = draw_members(args.held_out, args.seed + 1, args.length)
+    tr = run_trajectories(train_m, grid)
+    te = run_trajectories(test_m, grid)
+    x, y = features(train_m), targets(tr["z"], tr["closure"], args.steps)
+    model = Surrogate(seed=args.seed)
+    log = model.fit(x, y, steps=args.fit_steps)
+    xt = features(test_m)
+    model.predict(xt)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yp = model.predict(xt)
+    t_net = time.perf_counter() - t0
+    zp, cp = decode(yp, args.steps)
+    res = judge(zp, cp, te["z"], te["closure"], args.steps)
+    if args.save:
+        np.save(args.save, model.net.params())
+    out = {
+        "length": args.length, "steps": args.steps, "times": len(grid),
+        "train_runs": args.train, "held_out_runs": args.held_out,
+        "train_nonfinite": int(tr["nonfinite"].sum()),
+        "held_out_nonfinite": int(te["nonfinite"].sum()),
+        "solver_seconds_train": tr["seconds"],
+        "solver_seconds_held_out": te["seconds"],
+        "solver_glups_held_out": te["fluid_nodes"] * te["steps"] / te["seconds"] / 1e9,
+        "fit": {"steps": log.steps, "seconds": log.seconds,
+                "first_loss": log.first_loss, "last_loss": log.last_loss},
+        "network_seconds_held_out": t_net,
+        "speedup_vs_solver": te["seconds"] / max(t_net, 1e-9),
+        "judge": res,
+    }
+    print(json.dumps(out))
+    model.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

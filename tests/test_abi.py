@@ -38,8 +38,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_binding_lists_every_declared_symbol():
-    from paper_1309_6726_gb300 import lbm
-    assert set(lbm.SYMBOLS) == _declared()
+    from paper_1309_6726_gb300 import lbm, mlp
+    assert set(lbm.SYMBOLS) | set(mlp.SYMBOLS) == _declared()
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
@@ -65,3 +65,16 @@ def test_fit_reff_host_helper(lib):
     t = np.arange(1000, 6000, 250.0)
     assert lbm.fit_reff(t, 3.0 + v * t, gamma, mu, L, c) == pytest.approx(
         H / 2, rel=1e-12)
+
+
+def test_mlp_create_rejects_bad_shapes_without_touching_the_gpu(lib):
+    from paper_1309_6726_gb300 import lbm, mlp
+    L = mlp.load_library()
+    h = ctypes.c_void_p()
+    bad = mlp.Shape(4, 250, 3, 65, 64)  # hidden width not a multiple of 16
+    assert L.lbm_mlp_create(ctypes.byref(bad), ctypes.byref(h)) == lbm.LBM_EINVAL
+    assert b"shape" in L.lbm_mlp_last_error(None)
+    assert L.lbm_mlp_create(None, ctypes.byref(h)) == lbm.LBM_EINVAL
+    assert L.lbm_mlp_param_count(None) == -1
+    assert mlp.layer_shapes(4, 256, 3, 65) == [(256, 4), (256, 256),
+                                               (256, 256), (65, 256)]

@@ -3,8 +3,8 @@ relies on (Poiseuille flow between bounce-back walls, Laplace law, the 30
 degree contact angle, the linear Washburn law of Eq. 1) and its qualitative
 findings with reaction on (retardation, pore closure).
 
-Tolerances are stated with each test; the paper gives none (it says the LB
-reproduces Eq. 1 "accurately", Sec. III).
+Tolerances are stated with each test; the paper gives none (Sec. III only
+reports that the LB front follows Eq. 1 closely).
 """
 import math
 

@@ -1,0 +1,78 @@
+"""The surrogate end to end at a small scale: trajectories from the batched
+solver, training with the library's kernels, the solver as judge on
+held-out parameters, the solver as fallback outside the training domain,
+and what the network gains over running the solver."""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_surrogate_learns_solver_trajectories_and_saves_time():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1309_6726_gb300 import surrogate as S
+
+    length, steps = 96, 1500
+    grid = S.time_grid(steps, n=S.N_TIMES, t_first=20)
+    train_m = S.draw_members(320, seed=5, length=length)
+    test_m = S.draw_members(48, seed=6, length=length)
+    tr = S.run_trajectories(train_m, grid)
+    te = S.run_trajectories(test_m, grid)
+    assert tr["nonfinite"].sum() < 0.05 * len(train_m)
+    # the fronts move (closure needs longer horizons than this one)
+    assert np.nanmax(tr["z"][:, -1]) > 5.0
+
+    model = S.Surrogate(hidden=128, layers=3, seed=1, max_batch=512)
+    log = model.fit(S.features(train_m), S.targets(tr["z"], tr["closure"], steps),
+                    steps=3000, batch=320, lr=3e-3)
+    assert log.last_loss < 0.05 * log.first_loss
+
+    xt = S.features(test_m)
+    model.predict(xt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yp = model.predict(xt)
+    t_net = time.perf_counter() - t0
+    zp, cp = S.decode(yp, steps)
+    res = S.judge(zp, cp, te["z"], te["closure"], steps)
+    print(res, "solver %.3f s, network %.5f s" % (te["seconds"], t_net))
+    # a small training set at a short horizon: a looser bound than the
+    # 2 percent of the full-size run, but well below an untrained guess
+    assert res["front_rel_err_median"] < 0.10
+    assert res["closure_agreement"] > 0.8
+    # the gain: the answer for every held-out run, at that error, costs a
+    # forward pass instead of a solver run
+    assert te["seconds"] > 20 * t_net
+
+    # outside the training domain (another capillary length) the solver
+    # answers instead
+    other = S.draw_members(3, seed=7, length=length + 8)
+    z, c, src = S.predict_or_solve(model, other + test_m[:2], grid, length)
+    assert list(src) == ["solver"] * 3 + ["network"] * 2
+    ref = S.run_trajectories(other, grid)
+    np.testing.assert_array_equal(z[:3], ref["z"])
+    np.testing.assert_array_equal(c[:3], ref["closure"])
+    zn, cn = S.decode(model.predict(S.features(test_m[:2])), steps)
+    np.testing.assert_array_equal(z[3:], zn)
+    print("nonfinite runs: train %d/%d, held-out %d/%d, fallback %d/3" % (
+        tr["nonfinite"].sum(), len(train_m), te["nonfinite"].sum(),
+        len(test_m), ref["nonfinite"].sum()))
+    model.close()
+
+
+def test_time_grid_and_target_round_trip():
+    from paper_1309_6726_gb300 import surrogate as S
+    g = S.time_grid(20000)
+    assert g.size == 64 and g[0] == 100 and g[-1] == 20000
+    assert np.all(np.diff(g) > 0)
+    z = np.array([[1.0, 2.0], [3.0, np.nan]])
+    c = np.array([1234, -1])
+    y = S.targets(z, c, 20000)
+    zz, cc = S.decode(y, 20000)
+    np.testing.assert_allclose(zz[0], z[0], rtol=1e-6)
+    assert cc[0] == 1234 and cc[1] == -1
