@@ -767,8 +767,9 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
 extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
     if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
-    const int nb = (int)((h->ncols + 127) / 128);
-    k_obs_columns<<<nb, 128, 0, h->stream>>>(
+    // 32 columns per block, 8 warps splitting their rows
+    const int nb = (int)((h->ncols + 31) / 32);
+    k_obs_columns<<<nb, dim3(32, 8), 0, h->stream>>>(
         h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
         h->d_mom[h->cur], h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
     k_obs_reduce<<<h->count, 256, 0, h->stream>>>(

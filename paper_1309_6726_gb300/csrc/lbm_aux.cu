@@ -196,68 +196,109 @@ __global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
 }
 
 // ---------------------------------------------------------------------------
-// Observables.  Pass 1: one thread per column of every lattice (columns of
-// all lattices are numbered consecutively through col_base) walks the
-// column and writes a ColObs.  Pass 2: one block per lattice reduces them.
+// Observables.  Pass 1: blocks of 32 x 8 threads take 32 consecutive columns
+// of all lattices (numbered through col_base): lane = column, so loads
+// coalesce along rows, and the 8 warps split the rows of each column
+// (y = warp, warp + 8, ...); their partial results meet in shared memory
+// and are combined in a fixed order into one ColObs per column.
+// Pass 2: one block per lattice reduces the columns.
 // ---------------------------------------------------------------------------
 
-__global__ void k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
-                              const int64_t *col_base, int ncols_total,
-                              const void *fin, const __half *min_,
-                              const uint8_t *mask_all, const double *m_all,
-                              long long t, bool half, ColObs *out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols_total) return;
-    const int l = col_lat[c];
-    const LatDesc d = desc[l];
-    const int x = (int)(c - col_base[l]);
-    const MaskBits mb(t);
-    const uint8_t *mask = mask_all + d.node_off;
-    const int ny = d.ny;
-    const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
-    ColObs o = {};
-    int lo = -1;
-    bool below = true;
-    int b = 0, tt = 0;
-    float v[NPOP];
-    for (int y = 0; y < ny; ++y) {
-        const int64_t own = (int64_t)y * d.pitch + x;
-        const uint8_t s = mask[own];
-        const bool solid = s & mb.force;
-        if (solid) {
-            if (below) ++b;
-            ++tt;
-            if (!(s & mb.pull)) {  // turned solid at the end of the last step
-                pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
-                double ra = 0, rb = 0;
-                for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
-                o.pend_a += ra;
-                o.pend_b += rb;
-                o.pend_c += (double)v[18] + v[19] + v[20] + v[21];
-                o.pend_m += m_all[d.node_off + own];
+constexpr int OBS_ROWS = 8;  // warps per block in k_obs_columns
+
+struct ObsPart {
+    double mass[4], pend[4];
+    float phi0, phi1;
+    int h, fl0, fl1, nonfin, klo, khi;
+};
+
+__global__ void __launch_bounds__(32 * OBS_ROWS)
+    k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
+                  const int64_t *col_base, int ncols_total, const void *fin,
+                  const __half *min_, const uint8_t *mask_all,
+                  const double *m_all, long long t, bool half, ColObs *out) {
+    __shared__ ObsPart part[OBS_ROWS][32];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int c = blockIdx.x * 32 + lane;
+    ObsPart p = {};
+    p.klo = 0x7fffffff;  // lowest / highest fluid row: key = 2 y + phase
+    p.khi = -1;
+    int ny = 0;
+    if (c < ncols_total) {
+        const int l = col_lat[c];
+        const LatDesc d = desc[l];
+        const int x = (int)(c - col_base[l]);
+        const MaskBits mb(t);
+        const uint8_t *mask = mask_all + d.node_off;
+        ny = d.ny;
+        const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
+        float v[NPOP];
+        for (int y = w; y < ny; y += OBS_ROWS) {
+            const int64_t own = (int64_t)y * d.pitch + x;
+            const uint8_t s = mask[own];
+            if (s & mb.force) {
+                if (!(s & mb.pull)) {  // turned solid at the end of the last step
+                    pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+                    double ra = 0, rb = 0;
+                    for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+                    p.pend[0] += ra;
+                    p.pend[1] += rb;
+                    p.pend[2] += (double)v[18] + v[19] + v[20] + v[21];
+                    p.pend[3] += m_all[d.node_off + own];
+                }
+                continue;
             }
-            continue;
+            pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+            float ra = 0.f, rb = 0.f;
+            for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+            const float cc = v[18] + v[19] + v[20] + v[21];
+            if (!(ra + rb < 3.0e38f)) p.nonfin = 1;
+            p.mass[0] += ra;
+            p.mass[1] += rb;
+            p.mass[2] += cc;
+            p.mass[3] += m_all[d.node_off + own];
+            p.h += 1;
+            const int key = 2 * y + (ra > rb ? 1 : 0);
+            p.klo = min(p.klo, key);
+            p.khi = max(p.khi, key);
+            if (y == yc0) { p.phi0 = ra - rb; p.fl0 = 1; }
+            if (y == yc1) { p.phi1 = ra - rb; p.fl1 = 1; }
         }
-        below = false;
-        tt = 0;
-        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
-        float ra = 0.f, rb = 0.f;
-        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
-        const float cc = v[18] + v[19] + v[20] + v[21];
-        if (!(ra + rb < 3.0e38f)) o.nonfinite = 1;
-        o.mass_a += ra;
-        o.mass_b += rb;
-        o.mass_c += cc;
-        o.mass_m += m_all[d.node_off + own];
-        o.h += 1;
-        if (lo < 0) { lo = y; o.wet_lo = ra > rb; }
-        o.wet_hi = ra > rb;
-        if (y == yc0) { o.phi0 = ra - rb; o.fl0 = 1; }
-        if (y == yc1) { o.phi1 = ra - rb; o.fl1 = 1; }
     }
-    o.b = b;
-    o.t = tt;
-    if (o.h == 0) { o.b = ny; o.t = ny; o.wet_lo = o.wet_hi = 0; }
+    part[w][lane] = p;
+    __syncthreads();
+    if (w != 0 || c >= ncols_total) return;
+    ColObs o = {};
+    int klo = 0x7fffffff, khi = -1;
+    for (int k = 0; k < OBS_ROWS; ++k) {
+        const ObsPart &q = part[k][lane];
+        o.mass_a += q.mass[0];
+        o.mass_b += q.mass[1];
+        o.mass_c += q.mass[2];
+        o.mass_m += q.mass[3];
+        o.pend_a += q.pend[0];
+        o.pend_b += q.pend[1];
+        o.pend_c += q.pend[2];
+        o.pend_m += q.pend[3];
+        if (q.fl0) { o.phi0 = q.phi0; o.fl0 = 1; }
+        if (q.fl1) { o.phi1 = q.phi1; o.fl1 = 1; }
+        o.h += q.h;
+        o.nonfinite |= q.nonfin;
+        klo = min(klo, q.klo);
+        khi = max(khi, q.khi);
+    }
+    if (o.h == 0) {
+        o.b = ny;
+        o.t = ny;
+        o.wet_lo = o.wet_hi = 0;
+    } else {
+        // the walls are the solid runs below the lowest and above the
+        // highest fluid row
+        o.b = klo >> 1;
+        o.t = ny - 1 - (khi >> 1);
+        o.wet_lo = klo & 1;
+        o.wet_hi = khi & 1;
+    }
     out[c] = o;
 }
 

