@@ -42,6 +42,13 @@ METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated err
 BYTES_PER_NODE = {"fp32": 177.0, "fp16": 101.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
+#: DRAM bytes read + written per fluid-node update by the step kernel
+#: (default 64 x 8 tiles), from one ncu capture (dram__bytes_read.sum +
+#: dram__bytes_write.sum) of the first 40 capillaries of the sweep -- the
+#: 512-capillary state is too large to capture; traffic scales with the
+#: fluid nodes a launch updates.  Reported for the sweep at the default
+#: tile only.
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.57, "fp16": 105.75}
 
 
 def load_peaks():
@@ -343,6 +350,9 @@ def main():
                    "speedup_of_headline": (n_fluid * args.steps / (ms / 1e3)
                                            / 1e9) / g2}
     peak, peak_kind = load_peaks()
+    traffic = None
+    if args.workload == "sweep" and not os.environ.get("LBM_TILE"):
+        traffic = TRAFFIC_PER_FLUID_NODE[args.precision] * n_fluid
     bpn = BYTES_PER_NODE[args.precision] + DEPOSIT_BYTES * f_s
     achieved = n_fluid * bpn / (ms_step / 1e3) / 1e9
     e2e = None
@@ -372,9 +382,9 @@ def main():
                        "parallelism": "dp%d (independent capillaries)" % world},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind, "traffic": traffic,
                          "bytes_per_fluid_node": bpn,
-                         "kernel": "k_step (one launch per step)"},
+                         "kernel": "k_step_tma (one launch per step)"},
             "compare": compare,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": args.steps,

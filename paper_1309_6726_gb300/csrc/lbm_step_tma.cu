@@ -175,7 +175,8 @@ struct TmaTile {
     static_assert((TX * (int)sizeof(T)) % 16 == 0, "store box row");
     static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0, "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
-    static_assert(NRING <= NT && NRING / NW < 32, "ring spread");
+    static constexpr int RW = (NRING + NW - 1) / NW;  // ring cells per warp
+    static_assert(NRING <= NT && RW <= 32, "ring spread");
     static_assert(TX % 32 == 0, "a warp covers 32 columns of one row");
 };
 
@@ -444,10 +445,12 @@ __global__ void __launch_bounds__(TX *TY)
             fr[(ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : ra;
             fr[TT::RX * TT::RY + (ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : rb;
         }
-        // ring of the density frame, spread over the warps
+        // ring of the density frame, spread over the warps: the first RW
+        // lanes of each warp take RW consecutive ring cells (consecutive
+        // addresses, no shared-memory bank conflicts)
         {
-            const int r = lane * TT::NW + warp;
-            if (r < TT::NRING) {
+            const int r = warp * TT::RW + lane;
+            if (lane < TT::RW && r < TT::NRING) {
                 int ry, rx;
                 if (r < TT::RX) { ry = 0; rx = r; }
                 else if (r < 2 * TT::RX) { ry = TT::RY - 1; rx = r - TT::RX; }
