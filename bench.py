@@ -165,6 +165,18 @@ def surface_fraction(geoms) -> float:
     return surf / max(1, fluid_nodes(geoms))
 
 
+def combine_ranks(ms: float, n_fluid: int, device) -> tuple[float, float]:
+    """Across the ranks of the process group: the slowest rank's timed
+    region (max) and the fluid nodes all ranks updated per step (sum)."""
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    n = torch.tensor([float(n_fluid)], dtype=torch.float64, device=device)
+    td.all_reduce(n)
+    return float(t.item()), float(n.item())
+
+
 def time_gpu(geoms, params, precision, steps, warmup, dist):
     import torch
     from paper_1309_6726_gb300 import lbm
@@ -330,12 +342,7 @@ def main():
                        args.warmup, dist)
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(n_fluid)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tot)
-        n_fluid_all = float(tot.item())
+        ms, n_fluid_all = combine_ranks(ms, n_fluid, "cuda")
     else:
         n_fluid_all = float(n_fluid)
     ms_step = ms / args.steps
