@@ -41,6 +41,9 @@ __global__ void k_export(const LatDesc *, int, const void *, const __half *,
 __global__ void k_settle(const LatDesc *, int, const void *, const __half *,
                          uint8_t *, double *, LatState *, long long, bool);
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
+__global__ void k_mask_init(const LatDesc *, int, const uint8_t *, uint8_t *);
+__global__ void k_col_init(const LatDesc *, int, const uint8_t *, int32_t *,
+                           int16_t *);
 __global__ void k_obs_columns(const LatDesc *, const int32_t *,
                               const int64_t *, int, const void *,
                               const __half *, const uint8_t *,
@@ -501,34 +504,15 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     h->nsec = sec;
 
     std::vector<int32_t> tile_lat(tiles), col_lat(cols);
-    std::vector<int32_t> col_fluid(sec);
-    std::vector<int16_t> wall0(2 * sec);
-    std::vector<uint8_t> mask(node, 0);
     for (int l = 0; l < count; ++l) {
         const LatDesc &d = h->desc[l];
         const int nt = d.tiles_x * ((d.ny + h->ty - 1) / h->ty);
         for (int k = 0; k < nt; ++k) tile_lat[d.tile_base + k] = l;
         for (int x = 0; x < d.nx; ++x) col_lat[h->col_base[l] + x] = l;
-        const uint8_t *S = g[l].solid;
-        for (int y = -GHOST; y < d.ny + GHOST; ++y) {
-            const int ys = ((y % d.ny) + d.ny) % d.ny;  // periodic image
-            for (int x = -GHOST; x < d.nx + GHOST; ++x) {
-                const int xs = ((x % d.nx) + d.nx) % d.nx;
-                mask[d.node_off + (int64_t)y * d.pitch + x] =
-                    S[(int64_t)ys * d.nx + xs] ? 7 : 0;
-            }
-        }
-        for (int x = d.cap_x0; x < d.cap_x1; ++x) {
-            int fl = 0, b = 0, t = 0;
-            for (int y = 0; y < d.ny; ++y) fl += S[(int64_t)y * d.nx + x] == 0;
-            while (b < d.ny && S[(int64_t)b * d.nx + x]) ++b;
-            while (t < d.ny && S[(int64_t)(d.ny - 1 - t) * d.nx + x]) ++t;
-            const int64_t k = d.col_off + (x - d.cap_x0);
-            col_fluid[k] = fl;
-            wall0[2 * k] = (int16_t)std::min(b, 32767);
-            wall0[2 * k + 1] = (int16_t)std::min(t, 32767);
-        }
     }
+    // mask bytes, section-column counts and initial wall thicknesses are
+    // built on the device from each lattice's solid array (k_mask_init,
+    // k_col_init) below
 
     // ---- device allocations ----------------------------------------------
     const size_t esz = h->half ? sizeof(__half) : sizeof(float);
@@ -580,9 +564,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     bad(cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
     bad(cudaMemcpy(h->d_col_lat, col_lat.data(), cols * sizeof(int32_t), cudaMemcpyHostToDevice), "cols");
     bad(cudaMemcpy(h->d_col_base, h->col_base.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice), "colbase");
-    bad(cudaMemcpy(h->d_mask, mask.data(), node, cudaMemcpyHostToDevice), "mask");
-    bad(cudaMemcpy(h->d_col_fluid, col_fluid.data(), sec * sizeof(int32_t), cudaMemcpyHostToDevice), "colfluid");
-    bad(cudaMemcpy(h->d_wall0, wall0.data(), 2 * sec * sizeof(int16_t), cudaMemcpyHostToDevice), "wall0");
+    bad(cudaMemset(h->d_mask, 0, node), "memset");
     bad(cudaMemset(h->d_pop[0], 0, pop * esz), "memset");
     bad(cudaMemset(h->d_pop[1], 0, pop * esz), "memset");
     if (h->half) {
@@ -613,19 +595,29 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         bad(dalloc(&tmp, 3 * h->max_nodes), "alloc");
         bad(dalloc(&tsol, h->max_nodes), "alloc");
     }
+    // the memsets above ran on the legacy stream; the handle's stream does
+    // not wait for it
+    if (st == LBM_OK) bad(cudaDeviceSynchronize(), "sync");
+    // one lattice at a time through the staging buffers; stream order keeps
+    // a lattice's copies behind the previous lattice's kernels
     for (int l = 0; l < count && st == LBM_OK; ++l) {
         const LatDesc &d = h->desc[l];
         const size_t N = (size_t)d.nx * d.ny;
-        bad(cudaMemcpy(tmp, g[l].rho_a, N * 4, cudaMemcpyHostToDevice), "rho_a");
-        bad(cudaMemcpy(tmp + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice), "rho_b");
-        bad(cudaMemcpy(tmp + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice), "conc");
-        bad(cudaMemcpy(tsol, g[l].solid, N, cudaMemcpyHostToDevice), "solid");
+        bad(cudaMemcpyAsync(tmp, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
+        bad(cudaMemcpyAsync(tmp + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
+        bad(cudaMemcpyAsync(tmp + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
+        bad(cudaMemcpyAsync(tsol, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
+        k_mask_init<<<dim3((d.nx + 2 * GHOST + 127) / 128, d.ny + 2 * GHOST), 128, 0, s>>>(
+            h->d_desc, l, tsol, h->d_mask);
+        if (d.cap_x1 > d.cap_x0)
+            k_col_init<<<(d.cap_x1 - d.cap_x0 + 127) / 128, 128, 0, s>>>(
+                h->d_desc, l, tsol, h->d_col_fluid, h->d_wall0);
         dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
         k_rest_state<<<grid, blk, 0, s>>>(h->d_desc, l, tmp, tmp + N, tmp + 2 * N, tsol, h->d_canon);
         k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->d_mom[0], h->half);
         bad(cudaGetLastError(), "init kernels");
-        bad(cudaStreamSynchronize(s), "init sync");
     }
+    bad(cudaStreamSynchronize(s), "init sync");
     if (tmp) cudaFree(tmp);
     if (tsol) cudaFree(tsol);
     if (st != LBM_OK) {

@@ -66,6 +66,43 @@ __device__ __forceinline__ void store_node(void *fout, __half *mout,
     for (int k = 0; k < QS; ++k) f[d.pop_off + (2 * Q + k) * d.plane + own] = dq[k];
 }
 
+// Mask bytes of lattice l over its ghost band (columns -2 .. nx + 1, rows
+// -2 .. ny + 1; every image is its periodic source node) from the row-major
+// solid array of the lattice: solid -> all three time bits set.
+__global__ void k_mask_init(const LatDesc *desc, int l, const uint8_t *solid,
+                            uint8_t *mask_all) {
+    const LatDesc d = desc[l];
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GHOST;
+    const int y = (int)blockIdx.y - GHOST;
+    if (x >= d.nx + GHOST) return;
+    const int xs = wrapg(x, d.nx), ys = wrapg(y, d.ny);
+    mask_all[d.node_off + (int64_t)y * d.pitch + x] =
+        solid[(int64_t)ys * d.nx + xs] ? 7 : 0;
+}
+
+// Per section column of lattice l: fluid nodes, and the initial wall
+// thickness from below and from above (runs of solid from each edge).
+__global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
+                           int32_t *col_fluid, int16_t *wall0) {
+    const LatDesc d = desc[l];
+    const int x = d.cap_x0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= d.cap_x1) return;
+    int fl = 0, b = 0, t = 0;
+    bool below = true;
+    for (int y = 0; y < d.ny; ++y) {
+        const bool sv = solid[(int64_t)y * d.nx + x] != 0;
+        fl += !sv;
+        if (below && sv) ++b;
+        if (!sv) below = false;
+        t = sv ? t + 1 : 0;
+    }
+    if (fl == 0) t = d.ny;  // a fully solid column: both runs are the column
+    const int64_t k = d.col_off + (x - d.cap_x0);
+    col_fluid[k] = fl;
+    wall0[2 * k] = (int16_t)min(b, 32767);
+    wall0[2 * k + 1] = (int16_t)min(t, 32767);
+}
+
 // canonical layout of one lattice: [22][ny][nx] floats, no padding.
 __global__ void k_rest_state(const LatDesc *desc, int l, const float *rho_a,
                              const float *rho_b, const float *conc,
