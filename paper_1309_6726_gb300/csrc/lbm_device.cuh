@@ -164,8 +164,12 @@ __device__ __forceinline__ float dec_sol(float d, float ct) {
 // reference.  rho~ = f_0 / w_0 rounded to FP16 (the density times
 // 1 - 3/2 u.u at equilibrium), so every deviation is small.  The eight
 // moving deviations are rounded first; the rest deviation then carries
-// what their read-back values leave of the FP32 density, so rounding
-// creates no mass.
+// what their read-back values -- rounded exactly as readers round them --
+// leave of the FP32 density, so rounding creates no mass.  (Forming that
+// read-back sum as rt * sum w_i + sum 2^-10 w_i d_i instead, one fused
+// multiply-add per population, was measured to turn the mass drift of a
+// long FP16 run from +1.9e-4 to -2.7e-4: the per-population roundings are
+// not unbiased.)
 __device__ __forceinline__ __half enc9(const float f[Q], __half dq[Q]) {
     float r = 0.f;
 #pragma unroll

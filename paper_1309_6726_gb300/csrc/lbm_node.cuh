@@ -161,7 +161,10 @@ __device__ __forceinline__ bool fluid_update(
     float cAx, cAy, cBx, cBy, adx, ady;
     stencil9(rhoB_nb, cAx, cAy);  // A feels B
     stencil9(rhoA_nb, cBx, cBy);  // B feels A
-    {
+    if (snb == 0u) {  // no solid neighbour (most nodes): the stencil is 0
+        adx = 0.f;
+        ady = 0.f;
+    } else {
         float sv[Q];
 #pragma unroll
         for (int i = 1; i < Q; ++i) sv[i] = ((snb >> i) & 1u) ? 1.f : 0.f;
