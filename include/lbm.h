@@ -91,7 +91,7 @@ typedef struct lbm_params {
     double g_coh;         /* cohesion strength G_c */
     double g_ads;         /* adhesion strength g (A attracted for g > 0) */
     double k_r;           /* reaction-rate constant [lu/ts], >= 0 */
-    double m_threshold;   /* precipitated mass that turns a node solid */
+    double m_threshold;   /* precipitated mass that turns a node solid, > 0 */
     double c_in;          /* concentration imposed at the inlet column */
     double body_force_x;  /* uniform acceleration along x (checks only) */
     int32_t inlet;        /* 1: column x = 0 imposes c_in */
@@ -182,7 +182,9 @@ lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
                           void *host, size_t bytes);
 
 /* Replaces the post-streaming populations (LBM_FIELD_POPS) or the deposit
- * (LBM_FIELD_DEPOSIT) of lattice k.  Values at solid nodes are ignored. */
+ * (LBM_FIELD_DEPOSIT) of lattice k.  Values at solid nodes are ignored; a
+ * deposit outside [0, m_threshold) at a fluid node is LBM_EINVAL (such a
+ * node would already have turned solid). */
 lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
                           const void *host, size_t bytes);
 

@@ -158,6 +158,13 @@ orc_lattice *orc_create(const orc_params *p, int nx, int ny,
         orc_geq(conc[n], 0.0, 0.0, geq);
         for (int k = 0; k < QS; ++k) L->g[k * N + n] = geq[k];
     }
+    /* a section column that is solid from the start: closed at step 0 */
+    for (int x = p->cap_x0; x < p->cap_x1 && x < nx && L->closure_step < 0; ++x) {
+        int all = 1;
+        for (int y = 0; y < ny; ++y)
+            if (!L->solid[(size_t)y * nx + x]) { all = 0; break; }
+        if (all) L->closure_step = 0;
+    }
     return L;
 }
 

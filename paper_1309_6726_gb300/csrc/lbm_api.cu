@@ -43,7 +43,7 @@ __global__ void k_settle(const LatDesc *, int, const void *, const __half *,
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
 __global__ void k_mask_init(const LatDesc *, int, const uint8_t *, uint8_t *);
 __global__ void k_col_init(const LatDesc *, int, const uint8_t *, int32_t *,
-                           int16_t *);
+                           int16_t *, LatState *);
 __global__ void k_obs_columns(const LatDesc *, const int32_t *,
                               const int64_t *, int, const void *,
                               const __half *, const uint8_t *,
@@ -161,6 +161,13 @@ static bool valid_params(const lbm_params &p, std::string &why) {
         !std::isfinite(p.c_in) || !std::isfinite(p.body_force_x) ||
         std::isnan(p.m_threshold)) {
         why = "non-finite constant";
+        return false;
+    }
+    // Deposit only grows, by the reaction: with a positive threshold a node
+    // can only reach it in a step in which it reacts, which is where the
+    // step kernel tests it.
+    if (!(p.m_threshold > 0.0)) {
+        why = "m_threshold must be > 0";
         return false;
     }
     if (p.precision != LBM_FP32 && p.precision != LBM_FP16) {
@@ -611,7 +618,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
             h->d_desc, l, tsol, h->d_mask);
         if (d.cap_x1 > d.cap_x0)
             k_col_init<<<(d.cap_x1 - d.cap_x0 + 127) / 128, 128, 0, s>>>(
-                h->d_desc, l, tsol, h->d_col_fluid, h->d_wall0);
+                h->d_desc, l, tsol, h->d_col_fluid, h->d_wall0, h->d_st);
         dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
         k_rest_state<<<grid, blk, 0, s>>>(h->d_desc, l, tmp, tmp + N, tmp + 2 * N, tsol, h->d_canon);
         k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->d_mom[0], h->half);
@@ -869,8 +876,15 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
         const double *src = static_cast<const double *>(host);
         for (int y = 0; y < d.ny; ++y)
             for (int x = 0; x < d.nx; ++x)
-                if (!(raw[(size_t)y * d.pitch + x] & 7))
-                    m[(size_t)y * d.pitch + x] = src[(size_t)y * d.nx + x];
+                if (!(raw[(size_t)y * d.pitch + x] & 7)) {
+                    const double v = src[(size_t)y * d.nx + x];
+                    // a fluid node at or above the threshold would have
+                    // turned solid when its deposit crossed it
+                    if (!(v >= 0.0 && v < d.m_th))
+                        return fail(h, LBM_EINVAL,
+                                    "deposit outside [0, m_threshold) at a fluid node");
+                    m[(size_t)y * d.pitch + x] = v;
+                }
         CK(h, cudaMemcpyAsync(h->d_m + d.node_off, m.data(), rows_n * 8,
                               cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));

@@ -81,9 +81,10 @@ __global__ void k_mask_init(const LatDesc *desc, int l, const uint8_t *solid,
 }
 
 // Per section column of lattice l: fluid nodes, and the initial wall
-// thickness from below and from above (runs of solid from each edge).
+// thickness from below and from above (runs of solid from each edge); a
+// column solid from the start sets the lattice's closure step to 0.
 __global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
-                           int32_t *col_fluid, int16_t *wall0) {
+                           int32_t *col_fluid, int16_t *wall0, LatState *st) {
     const LatDesc d = desc[l];
     const int x = d.cap_x0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= d.cap_x1) return;
@@ -96,7 +97,10 @@ __global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
         if (!sv) below = false;
         t = sv ? t + 1 : 0;
     }
-    if (fl == 0) t = d.ny;  // a fully solid column: both runs are the column
+    if (fl == 0) {
+        t = d.ny;  // a fully solid column: both runs are the column
+        atomicMin(&st[l].closure, 0ull);  // closed from the start: step 0
+    }
     const int64_t k = d.col_off + (x - d.cap_x0);
     col_fluid[k] = fl;
     wall0[2 * k] = (int16_t)min(b, 32767);

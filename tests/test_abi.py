@@ -78,3 +78,51 @@ def test_mlp_create_rejects_bad_shapes_without_touching_the_gpu(lib):
     assert L.lbm_mlp_param_count(None) == -1
     assert mlp.layer_shapes(4, 256, 3, 65) == [(256, 4), (256, 256),
                                                (256, 256), (65, 256)]
+
+
+def test_create_rejects_degenerate_parameters_without_touching_the_gpu(lib):
+    # every check runs before any CUDA call
+    import numpy as np
+    from paper_1309_6726_gb300 import inputs as I, lbm
+    L = lbm.load_library()
+    geom = I.capillary(40, 8, 8, 8)
+    keep = []
+
+    def arr(a, t):
+        a = np.ascontiguousarray(a, t)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8 if t == np.uint8
+                                               else ctypes.c_float))
+
+    def geo(nx=geom.nx, ny=geom.ny, x0=geom.cap_x0, x1=geom.cap_x1):
+        return lbm.Geometry(nx, ny, arr(geom.solid, np.uint8),
+                            arr(geom.rho_a, np.float32),
+                            arr(geom.rho_b, np.float32),
+                            arr(geom.conc, np.float32), x0, x1)
+
+    def params(**kw):
+        d = I.ModelParams().as_dict()
+        d.update(kw)
+        return lbm._params(d, kw.pop("precision", 0))
+
+    h = ctypes.c_void_p()
+    cases = [
+        (geo(), params(m_threshold=0.0), b"m_threshold"),
+        (geo(), params(tau_a=0.5), b"relaxation"),
+        (geo(), params(k_r=-1e-3), b"k_r"),
+        (geo(), params(g_coh=float("nan")), b"non-finite"),
+        (geo(ny=2), params(), b"ny >= 3"),
+        (geo(nx=0), params(), b"nx >= 1"),
+        (geo(x0=5, x1=5), params(), b"section"),
+        (geo(nx=20000, ny=20000), params(), b"too large"),
+    ]
+    for g, p, msg in cases:
+        assert L.lbm_create(ctypes.byref(g), ctypes.byref(p),
+                            ctypes.byref(h)) == lbm.LBM_EINVAL, msg
+        assert msg in L.lbm_last_error(None), (msg, L.lbm_last_error(None))
+    # a batch may not mix storage precisions; an empty batch is refused
+    G2 = (lbm.Geometry * 2)(geo(), geo())
+    P2 = (lbm.Params * 2)(params(), lbm._params(I.ModelParams().as_dict(), 1))
+    assert L.lbm_create_batch(G2, P2, 2, ctypes.byref(h)) == lbm.LBM_EINVAL
+    assert b"mixed precision" in L.lbm_last_error(None)
+    assert L.lbm_create_batch(G2, P2, 0, ctypes.byref(h)) == lbm.LBM_EINVAL
