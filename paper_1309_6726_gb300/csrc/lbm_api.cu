@@ -41,6 +41,8 @@ __global__ void k_export(const LatDesc *, int, const void *, const __half *,
 __global__ void k_settle(const LatDesc *, int, const void *, const __half *,
                          uint8_t *, double *, LatState *, long long, bool);
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
+__global__ void k_solid_mask(const LatDesc *, int, const uint8_t *, uint8_t,
+                             uint8_t *);
 __global__ void k_mask_init(const LatDesc *, int, const uint8_t *, uint8_t *);
 __global__ void k_col_init(const LatDesc *, int, const uint8_t *, int32_t *,
                            int16_t *, LatState *);
@@ -763,9 +765,9 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
 extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
     if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
-    // 32 columns per block, 8 warps splitting their rows
+    // 32 columns per block, OBS_ROWS warps splitting their rows
     const int nb = (int)((h->ncols + 31) / 32);
-    k_obs_columns<<<nb, dim3(32, 8), 0, h->stream>>>(
+    k_obs_columns<<<nb, dim3(32, OBS_ROWS), 0, h->stream>>>(
         h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
         h->d_mom[h->cur], h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
     k_obs_reduce<<<h->count, 256, 0, h->stream>>>(
@@ -793,15 +795,14 @@ extern "C" lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k,
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     const LatDesc &d = h->desc[k];
     if (n != (size_t)d.nx * d.ny) return fail(h, LBM_EINVAL, "size mismatch");
-    const size_t rows_bytes = (size_t)d.ny * d.pitch;
-    std::vector<uint8_t> raw(rows_bytes);
-    CK(h, cudaMemcpyAsync(raw.data(), h->d_mask + d.node_off, rows_bytes,
-                          cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    // extracted on the device into the export scratch (max_nodes floats)
     const MaskBits mb(h->steps);
-    for (int y = 0; y < d.ny; ++y)
-        for (int x = 0; x < d.nx; ++x)
-            host[(size_t)y * d.nx + x] = (raw[(size_t)y * d.pitch + x] & mb.force) ? 1 : 0;
+    uint8_t *tmp = reinterpret_cast<uint8_t *>(h->d_canon);
+    k_solid_mask<<<dim3((d.nx + 127) / 128, d.ny), 128, 0, h->stream>>>(
+        h->d_desc, k, h->d_mask, mb.force, tmp);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(host, tmp, n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 

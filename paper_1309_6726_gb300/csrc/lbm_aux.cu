@@ -107,6 +107,19 @@ __global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
     wall0[2 * k + 1] = (int16_t)min(t, 32767);
 }
 
+// Solid mask of lattice l at the current step (force bit), row-major
+// [ny][nx] bytes 0/1.
+__global__ void k_solid_mask(const LatDesc *desc, int l,
+                             const uint8_t *mask_all, uint8_t force,
+                             uint8_t *out) {
+    const LatDesc d = desc[l];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= d.nx) return;
+    out[(int64_t)y * d.nx + x] =
+        (mask_all[d.node_off + (int64_t)y * d.pitch + x] & force) ? 1 : 0;
+}
+
 // canonical layout of one lattice: [22][ny][nx] floats, no padding.
 __global__ void k_rest_state(const LatDesc *desc, int l, const float *rho_a,
                              const float *rho_b, const float *conc,
@@ -244,8 +257,6 @@ __global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
 // and are combined in a fixed order into one ColObs per column.
 // Pass 2: one block per lattice reduces the columns.
 // ---------------------------------------------------------------------------
-
-constexpr int OBS_ROWS = 8;  // warps per block in k_obs_columns
 
 struct ObsPart {
     double mass[4], pend[4];

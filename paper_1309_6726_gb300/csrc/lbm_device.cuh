@@ -132,6 +132,7 @@ struct StepArgs {
 };
 
 constexpr int GHOST = 2;  // ghost rows on each side in y
+constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
 // ---- FP16 storage codec ------------------------------------------------------
 // A component's populations are kept as FP16 deviations from a per-node
