@@ -22,9 +22,11 @@ cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
                                int ty, bool half, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
+                            const CUtensorMap *rest_maps,
                             const CUtensorMap *mask_maps,
                             const CUtensorMap *out_maps,
                             const CUtensorMap *out_mom_maps,
+                            const CUtensorMap *out_rest_maps,
                             const TileRec *sched, int nslots, int grid, int tx,
                             int ty, bool half, int *err, cudaStream_t s);
 cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
@@ -218,17 +220,20 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     }
     const int count = h->count;
     const size_t esz = h->half ? 2 : 4;
-    std::vector<CUtensorMap> maps(4 * count), moms(4 * count);
+    // moms: [2 buffers][count] reference copies, [2][count] reference
+    // stores, [2][count] rest-plane copies, [2][count] rest-plane stores
+    std::vector<CUtensorMap> maps(4 * count), moms(8 * count);
+    const cuuint64_t npl = h->half ? NP16 : NPOP;
     const CUtensorMapDataType pty =
         h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int b = 0; b < 2; ++b) {
         for (int l = 0; l < count; ++l) {
             const LatDesc &d = h->desc[l];
             const cuuint64_t rows = (cuuint64_t)(d.ny + 2 * GHOST);
-            cuuint64_t dims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NPOP};
+            cuuint64_t dims[3] = {(cuuint64_t)d.pitch, rows, npl};
             cuuint64_t strides[2] = {(cuuint64_t)d.pitch * esz, (cuuint64_t)d.plane * esz};
             cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx, h->half),
-                                 (cuuint32_t)(h->ty + 4), (cuuint32_t)NPOP};
+                                 (cuuint32_t)(h->ty + 4), (cuuint32_t)npl};
             cuuint32_t es[3] = {1, 1, 1};
             void *base = (char *)h->d_pop[b] +
                          (size_t)(d.pop_off - GHOST * d.pitch - XGHOST) * esz;
@@ -260,8 +265,8 @@ static bool make_maps(lbm_handle *h, std::string &why) {
             }
             // output: the lattice's own nodes, logical (0, 0) at the base
             // (16-byte aligned: the ghost band is 16 columns wide)
-            cuuint64_t odims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NPOP};
-            cuuint32_t obox[3] = {(cuuint32_t)h->tx, (cuuint32_t)h->ty, (cuuint32_t)NPOP};
+            cuuint64_t odims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, npl};
+            cuuint32_t obox[3] = {(cuuint32_t)h->tx, (cuuint32_t)h->ty, (cuuint32_t)npl};
             r = enc(&maps[(2 + b) * count + l], pty, 3,
                     (char *)h->d_pop[b] + (size_t)d.pop_off * esz, odims, strides,
                     obox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -281,6 +286,30 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
                 if (r != CUDA_SUCCESS) {
                     why = "cuTensorMapEncodeTiled failed for the moment output, code " +
+                          std::to_string((int)r);
+                    return false;
+                }
+                // FP32 rest planes after the 3 reference planes of the block
+                const int64_t g0 = (int64_t)GHOST * d.pitch + XGHOST;
+                char *rbase = (char *)h->d_mom[b] +
+                              (size_t)((d.mom_off - g0) + NMOM * d.plane) * 2;
+                cuuint64_t rstr[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane * 4};
+                cuuint64_t rdims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NREST};
+                cuuint32_t rbox[3] = {box[0], box[1], (cuuint32_t)NREST};
+                r = enc(&moms[(4 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        rbase, rdims, rstr, rbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                cuuint64_t rodims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NREST};
+                cuuint32_t robox[3] = {obox[0], obox[1], (cuuint32_t)NREST};
+                if (r == CUDA_SUCCESS)
+                    r = enc(&moms[(6 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            rbase + (size_t)g0 * 4, rodims, rstr, robox, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    why = "cuTensorMapEncodeTiled failed for the rest planes, code " +
                           std::to_string((int)r);
                     return false;
                 }
@@ -485,8 +514,8 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.mom_off = mom + GHOST * d.pitch + XGHOST;
         d.col_off = sec;
         node += d.plane;
-        pop += NPOP * d.plane;
-        mom += NMOM * d.plane;
+        pop += (h->half ? NP16 : NPOP) * d.plane;
+        mom += MOM_BLOCK * d.plane;
         h->col_base[l] = cols;
         cols += d.nx;
         sec += G.cap_x1 - G.cap_x0;
@@ -686,13 +715,13 @@ static StepArgs step_args(lbm_handle *h) {
 // One launch of the TMA step kernel reading buffer cur, writing cur ^ 1.
 static cudaError_t launch_tma(lbm_handle *h) {
     const int c = h->count, in = h->cur, out = h->cur ^ 1;
+    const CUtensorMap *m = h->d_mom_maps;  // see make_maps for its blocks
     return launch_step_tma(
-        step_args(h), h->d_maps + in * c,
-        h->half ? h->d_mom_maps + in * c : nullptr, h->d_mask_maps,
-        h->d_maps + (2 + out) * c,
-        h->half ? h->d_mom_maps + (2 + out) * c : nullptr, h->d_sched,
-        h->sched_slots, h->sched_grid, h->tx, h->ty, h->half, h->d_err,
-        h->stream);
+        step_args(h), h->d_maps + in * c, h->half ? m + in * c : nullptr,
+        h->half ? m + (4 + in) * c : nullptr, h->d_mask_maps,
+        h->d_maps + (2 + out) * c, h->half ? m + (2 + out) * c : nullptr,
+        h->half ? m + (6 + out) * c : nullptr, h->d_sched, h->sched_slots,
+        h->sched_grid, h->tx, h->ty, h->half, h->d_err, h->stream);
 }
 
 static cudaError_t launch_one(lbm_handle *h) {
@@ -896,7 +925,7 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
 
 // ---- checkpoints -----------------------------------------------------------
 
-static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '2'};
 
 struct CkptHeader {
     char magic[8];

@@ -8,7 +8,7 @@
 // therefore one pull away; "unstream" is its exact inverse:
 //   f*_i(x) = f_i(x + e_i)        if x + e_i is fluid,
 //   f*_i(x) = f_{opp i}(x)        if x + e_i is solid (it bounced back).
-#include "lbm_device.cuh"
+#include "lbm_node.cuh"
 
 namespace lbmk {
 
@@ -16,7 +16,10 @@ __device__ __forceinline__ float load_pop(const void *base, const __half *mom,
                                           const LatDesc &d, bool half, int q,
                                           int64_t e) {
     if (!half) return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
-    const float dv = __half2float(static_cast<const __half *>(base)[d.pop_off + q * d.plane + e]);
+    if (q == 0 || q == Q)  // rest populations: FP32, in the moment block
+        return rest_planes(mom, d)[(q == Q ? d.plane : 0) + e];
+    const float dv =
+        __half2float(static_cast<const __half *>(base)[d.pop_off + sp16(q) * d.plane + e]);
     const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
     const float rt = __half2float(mom[d.mom_off + comp * d.plane + e]);
     return comp < 2 ? dec_pop(q - comp * Q, dv, rt) : dec_sol(dv, rt);
@@ -51,19 +54,14 @@ __device__ __forceinline__ void pull_node(const void *fin, const __half *mom,
 __device__ __forceinline__ void store_node(void *fout, __half *mout,
                                            const LatDesc &d, bool half,
                                            int64_t own, const float v[NPOP]) {
-    if (!half) {
-        float *f = static_cast<float *>(fout);
-        for (int q = 0; q < NPOP; ++q) f[d.pop_off + q * d.plane + own] = v[q];
-        return;
-    }
-    __half *f = static_cast<__half *>(fout);
-    __half dq[Q];
-    for (int comp = 0; comp < 2; ++comp) {
-        mout[d.mom_off + comp * d.plane + own] = enc9(v + comp * Q, dq);
-        for (int i = 0; i < Q; ++i) f[d.pop_off + (comp * Q + i) * d.plane + own] = dq[i];
-    }
-    mout[d.mom_off + 2 * d.plane + own] = enc4(v + 2 * Q, dq);
-    for (int k = 0; k < QS; ++k) f[d.pop_off + (2 * Q + k) * d.plane + own] = dq[k];
+    const int pl = (int)d.plane;
+    if (!half)
+        store22_f32(static_cast<float *>(fout) + d.pop_off + own, pl, v, v + Q,
+                    v + 2 * Q);
+    else
+        store22_f16(static_cast<__half *>(fout) + d.pop_off + own,
+                    mout + d.mom_off + own, rest_planes(mout, d) + own, pl, pl,
+                    v, v + Q, v + 2 * Q);
 }
 
 // Mask bytes of lattice l over its ghost band (columns -2 .. nx + 1, rows

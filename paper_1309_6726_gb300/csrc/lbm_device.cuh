@@ -3,11 +3,14 @@
 //
 // Layout in HBM (one handle, `count` lattices packed back to back):
 //   populations: two ping-pong buffers; in each, lattice l owns 22
-//     consecutive planes of ny*pitch elements (A: 9, B: 9, solute: 4),
-//     rows padded to `pitch` (a multiple of 32 elements, so every row
+//     consecutive planes of (ny + 4) * pitch elements (A: 9, B: 9, solute:
+//     4), rows padded to `pitch` (a multiple of 32 elements, so every row
 //     starts on a 128-byte boundary in FP32 storage);
-//   FP16 storage adds 3 moment planes per lattice and buffer (rho_A,
-//     rho_B, C rounded to FP16) that the deviations are taken from;
+//   FP16 storage keeps 20 FP16 planes per lattice (the 8 moving A and 8
+//     moving B populations, then the 4 solute ones, see sp16) and, per
+//     lattice and buffer, a moment block of 3 FP16 reference planes
+//     (rho~_A, rho~_B, C~) followed by 2 FP32 planes holding the rest
+//     populations of A and B (rest_planes);
 //   every plane (populations, moments, mask) has a two-node ghost band
 //     around the lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx,
 //     nx + 1 -- holding the periodic images of the nodes next to the
@@ -32,7 +35,16 @@ namespace lbmk {
 constexpr int Q = 9;      // D2Q9 per fluid component
 constexpr int QS = 4;     // D2Q4 solute
 constexpr int NPOP = 22;  // 9 + 9 + 4 planes per lattice
-constexpr int NMOM = 3;   // FP16 storage: rho_A, rho_B, C planes
+constexpr int NMOM = 3;   // FP16 storage: rho~_A, rho~_B, C~ planes
+constexpr int NP16 = 20;  // FP16 storage: population planes (no rest ones)
+constexpr int NREST = 2;  // FP16 storage: FP32 rest planes of A and B
+// FP16 storage: the moment block of a lattice spans 7 half-planes, the 3
+// FP16 references then the 2 FP32 rest planes
+constexpr int MOM_BLOCK = NMOM + 2 * NREST;
+
+// FP16 storage plane of population q (A: 1..8, B: 10..17, solute 18..21;
+// the rest populations 0 and 9 are FP32, in the moment block)
+__host__ __device__ constexpr int sp16(int q) { return q < Q ? q - 1 : q - 2; }
 
 // D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
 __host__ __device__ __forceinline__ constexpr int cx(int i) {
@@ -135,56 +147,52 @@ constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
 // ---- FP16 storage codec ------------------------------------------------------
-// A component's populations are kept as FP16 deviations from a per-node
-// reference rho~ (FP16, stored once per node and component):
+// A component's moving populations are kept as FP16 deviations from a
+// per-node reference rho~ (FP16, stored once per node and component), the
+// solute likewise; the rest population is kept in FP32:
 //   moving i = 1..8:  d = 2^10 (f_i / w_i - rho~),  f_i = w_i (rho~ + 2^-10 d)
-//   rest:             d = 2^12 (f_0 - w_0 rho~),    f_0 = w_0 rho~ + 2^-12 d
 //   solute k = 0..3:  d = 2^10 (4 g_k - C~),        g_k = (C~ + 2^-10 d) / 4
-// The power-of-two scales are exact; they lift the minority component's
-// small deviations out of FP16's subnormal range (|d| stays far below
-// 65504).  The rest population's scale is a power of two rather than a
-// weight so that the writer can solve for it without a division.  Every
-// read rounds exactly as written here (no contraction into later sums), so
-// all code paths rebuild the same FP32 value from the same bits.
+//   rest:             f_0 in FP32, the density minus the moving read-backs
+// The power-of-two scale is exact; it lifts the minority component's small
+// deviations out of FP16's subnormal range (|d| stays far below 65504).
+// Every read rounds exactly as written here (no contraction into later
+// sums), so all code paths rebuild the same FP32 value from the same bits.
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
-constexpr float kRestScale = 4096.0f;
-constexpr float kInvRestScale = 1.0f / 4096.0f;
 
-// Population i (0..8) of a D2Q9 component from its deviation and reference.
+// Moving population i (1..8) of a D2Q9 component from its deviation and
+// reference.
 __device__ __forceinline__ float dec_pop(int i, float d, float rt) {
-    return i == 0 ? __fmaf_rn(d, kInvRestScale, __fmul_rn(wq(0), rt))
-                  : __fmul_rn(wq(i), __fmaf_rn(d, kInvDevScale, rt));
+    return __fmul_rn(wq(i), __fmaf_rn(d, kInvDevScale, rt));
 }
 // A solute population from its deviation and reference.
 __device__ __forceinline__ float dec_sol(float d, float ct) {
     return __fmul_rn(0.25f, __fmaf_rn(d, kInvDevScale, ct));
 }
 
-// Encodes the 9 post-collision populations of one component; returns the
+// Encodes the 9 post-collision populations of one component: the moving
+// deviations into dq[1..8], the rest population into `rest`; returns the
 // reference.  rho~ = f_0 / w_0 rounded to FP16 (the density times
-// 1 - 3/2 u.u at equilibrium), so every deviation is small.  The eight
-// moving deviations are rounded first; the rest deviation then carries
-// what their read-back values -- rounded exactly as readers round them --
-// leave of the FP32 density, so rounding creates no mass.  (Forming that
-// read-back sum as rt * sum w_i + sum 2^-10 w_i d_i instead, one fused
-// multiply-add per population, was measured to turn the mass drift of a
-// long FP16 run from +1.9e-4 to -2.7e-4: the per-population roundings are
-// not unbiased.)
-__device__ __forceinline__ __half enc9(const float f[Q], __half dq[Q]) {
-    float r = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r += f[i];
+// 1 - 3/2 u.u at equilibrium), so every deviation is small.  The rest
+// population takes up the quantisation error of the eight moving ones --
+// each error f_i - read-back(f_i) is exact in FP32 and tiny, and readers
+// round the read-back exactly as here -- so the stored mass is the FP32
+// mass up to one rounding at f_0's magnitude.  (Solving the rest
+// population from an FP32 sum of all nine values instead biased the mass
+// of long runs by about 1e-8 per step: populations near w_i rho share
+// their low-order bits, so the roundings of such sums are not unbiased.)
+__device__ __forceinline__ __half enc9(const float f[Q], __half dq[Q],
+                                       float &rest) {
     const __half rh = __float2half_rn(f[0] * (1.0f / wq(0)));
     const float rt = __half2float(rh);
     const float nrt = -kDevScale * rt;
-    float moving = 0.f;
+    float err = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         dq[i] = __float2half_rn(__fmaf_rn(f[i], kDevScale / wq(i), nrt));
-        moving += dec_pop(i, __half2float(dq[i]), rt);
+        err += f[i] - dec_pop(i, __half2float(dq[i]), rt);
     }
-    dq[0] = __float2half_rn(((r - moving) - __fmul_rn(wq(0), rt)) * kRestScale);
+    rest = f[0] + err;
     return rh;
 }
 
@@ -212,6 +220,19 @@ __device__ __forceinline__ float rcp_nr(float x) {
 }
 
 constexpr int XGHOST = 16;  // physical columns before logical column 0
+
+// FP16 storage: the FP32 rest planes of lattice d (A, then B, `plane`
+// apart), at its logical node (0, 0), inside the moment block that starts
+// 3 planes before them.  Both the block start (a multiple of 7 planes of
+// halves) and the 3 reference planes keep them 16-byte aligned.
+__device__ __forceinline__ float *rest_planes(__half *mom, const LatDesc &d) {
+    const int64_t g = (int64_t)GHOST * d.pitch + XGHOST;
+    return reinterpret_cast<float *>(mom + (d.mom_off - g) + NMOM * d.plane) + g;
+}
+__device__ __forceinline__ const float *rest_planes(const __half *mom,
+                                                    const LatDesc &d) {
+    return rest_planes(const_cast<__half *>(mom), d);
+}
 
 // Calls f(offset) for every periodic image of node (x, y) that lies in the
 // ghost band (columns -2 .. nx + 1, rows -2 .. ny + 1, the node itself

@@ -82,34 +82,42 @@ __device__ __forceinline__ void stencil9(const float v[Q], float &sx_,
     sy_ = wq(1) * (v[2] - v[4]) + wq(5) * (d1 - d2);
 }
 
-template <class S>
-__device__ __forceinline__ void store9(typename S::T *__restrict__ p,
-                                       __half *__restrict__ mp, int plane,
-                                       const float f[Q]) {
-    if constexpr (!S::kHalf) {
+// FP32 storage: the 22 values of a node at p[q * plane].
+__device__ __forceinline__ void store22_f32(float *__restrict__ p, int plane,
+                                            const float fA[Q],
+                                            const float fB[Q],
+                                            const float g[QS]) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) p[i * plane] = f[i];
-    } else {
-        __half dq[Q];
-        *mp = enc9(f, dq);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) p[i * plane] = dq[i];
+    for (int i = 0; i < Q; ++i) {
+        p[i * plane] = fA[i];
+        p[(Q + i) * plane] = fB[i];
     }
+#pragma unroll
+    for (int k = 0; k < QS; ++k) p[(2 * Q + k) * plane] = g[k];
 }
 
-template <class S>
-__device__ __forceinline__ void store4(typename S::T *__restrict__ p,
-                                       __half *__restrict__ mp, int plane,
-                                       const float g[QS]) {
-    if constexpr (!S::kHalf) {
+// FP16 storage: the 20 FP16 deviations of a node at p[sp16(q) * plane],
+// its 3 references at mp[c * plane] and its 2 FP32 rest populations at
+// rp[c * rplane].
+__device__ __forceinline__ void store22_f16(__half *__restrict__ p,
+                                            __half *__restrict__ mp,
+                                            float *__restrict__ rp, int plane,
+                                            int rplane, const float fA[Q],
+                                            const float fB[Q],
+                                            const float g[QS]) {
+    __half dq[Q];
+    float rest;
+    mp[0] = enc9(fA, dq, rest);
+    rp[0] = rest;
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[k * plane] = g[k];
-    } else {
-        __half dq[QS];
-        *mp = enc4(g, dq);
+    for (int i = 1; i < Q; ++i) p[sp16(i) * plane] = dq[i];
+    mp[plane] = enc9(fB, dq, rest);
+    rp[rplane] = rest;
 #pragma unroll
-        for (int k = 0; k < QS; ++k) p[k * plane] = dq[k];
-    }
+    for (int i = 1; i < Q; ++i) p[sp16(Q + i) * plane] = dq[i];
+    mp[2 * plane] = enc4(g, dq);
+#pragma unroll
+    for (int k = 0; k < QS; ++k) p[sp16(2 * Q + k) * plane] = dq[k];
 }
 
 // Writes the 22 post-collision values of a node at plane offset `off`.
@@ -119,25 +127,29 @@ __device__ __forceinline__ void store_node22(const StepArgs &a,
                                              const float fA[Q],
                                              const float fB[Q],
                                              const float g[QS]) {
-    using T = typename S::T;
     const int pl = (int)d.plane;
-    T *p = static_cast<T *>(a.fout) + d.pop_off + off;
-    __half *mp = S::kHalf ? a.mout + d.mom_off + off : nullptr;
-    store9<S>(p, mp, pl, fA);
-    store9<S>(p + Q * pl, S::kHalf ? mp + pl : nullptr, pl, fB);
-    store4<S>(p + 2 * Q * pl, S::kHalf ? mp + 2 * pl : nullptr, pl, g);
+    if constexpr (!S::kHalf) {
+        store22_f32(static_cast<float *>(a.fout) + d.pop_off + off, pl, fA, fB, g);
+    } else {
+        store22_f16(static_cast<__half *>(a.fout) + d.pop_off + off,
+                    a.mout + d.mom_off + off, rest_planes(a.mout, d) + off, pl,
+                    pl, fA, fB, g);
+    }
 }
 
 // Writes the 22 post-collision values of the tile node at `o` (planes NT
-// apart) -- a shared-memory tile that a bulk tensor store then copies out.
+// apart) -- a shared-memory tile that bulk tensor stores then copy out:
+// FP32 [22][NT]; FP16 [20][NT] deviations, om [3][NT] references, orest
+// [2][NT] rest populations.
 template <class S, int NT>
 __device__ __forceinline__ void store_tile22(typename S::T *o, __half *om,
-                                             const float fA[Q],
+                                             float *orest, const float fA[Q],
                                              const float fB[Q],
                                              const float g[QS]) {
-    store9<S>(o, om, NT, fA);
-    store9<S>(o + Q * NT, S::kHalf ? om + NT : nullptr, NT, fB);
-    store4<S>(o + 2 * Q * NT, S::kHalf ? om + 2 * NT : nullptr, NT, g);
+    if constexpr (!S::kHalf)
+        store22_f32(o, NT, fA, fB, g);
+    else
+        store22_f16(o, om, orest, NT, NT, fA, fB, g);
 }
 
 // Everything after the pull, for a node that is fluid in s_t.

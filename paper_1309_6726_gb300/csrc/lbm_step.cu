@@ -61,13 +61,16 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
         const int syy = cy(i) > 0 ? gym : (cy(i) < 0 ? gyp : gy);
         const bool b = (bb >> i) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
-        const int q = comp * Q + (b ? opp(i) : i);
+        const int qi = b ? opp(i) : i;
+        const int q = comp * Q + qi;
         if constexpr (!S::kHalf) {
             f[i] = __ldg(fin + d.pop_off + q * d.plane + src);
+        } else if (i == 0) {
+            f[0] = rest_planes(mom, d)[comp * d.plane + own];
         } else {
-            const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
+            const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
             const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
-            f[i] = dec_pop(i, dv, rt);
+            f[i] = dec_pop(qi, dv, rt);
         }
     }
 }
@@ -91,7 +94,7 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
         if constexpr (!S::kHalf) {
             g[k] = __ldg(fin + d.pop_off + q * d.plane + src);
         } else {
-            const float dv = __half2float(fin[d.pop_off + q * d.plane + src]);
+            const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
             const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
             g[k] = dec_sol(dv, ct);
         }

@@ -143,13 +143,19 @@ struct TmaTile {
     static constexpr int PL = BX * BY;            // elements per plane
     static constexpr int MXO = 16;                // mask box: 16-byte aligned
     static constexpr int MBX = TX + 2 * MXO;
-    static constexpr int POP_BYTES = NPOP * PL * (int)sizeof(T);
+    // population planes in a stage: 22 FP32, or 20 FP16 deviations plus
+    // 3 FP16 references and 2 FP32 rest planes
+    static constexpr int NPL = S::kHalf ? NP16 : NPOP;
+    static constexpr int POP_BYTES = NPL * PL * (int)sizeof(T);
     static constexpr int MOM_BYTES = S::kHalf ? NMOM * PL * 2 : 0;
+    static constexpr int REST_BYTES = S::kHalf ? NREST * PL * 4 : 0;
+    static constexpr int REST_OFF = POP_BYTES + MOM_BYTES;  // within a stage
     static constexpr int MASK_BYTES = (MBX * BY + 127) / 128 * 128;
     static constexpr int STAGE =
-        ((POP_BYTES + MOM_BYTES + 127) / 128 * 128) + MASK_BYTES;
+        ((POP_BYTES + MOM_BYTES + REST_BYTES + 127) / 128 * 128) + MASK_BYTES;
     static constexpr int MASK_OFF = STAGE - MASK_BYTES;  // within a stage
-    static constexpr int TX_BYTES = POP_BYTES + MOM_BYTES + MBX * BY + 128;
+    static constexpr int TX_BYTES =
+        POP_BYTES + MOM_BYTES + REST_BYTES + MBX * BY + 128;
     static constexpr int RX = TX + 2, RY = TY + 2;  // density frame
     static constexpr int NRING = 2 * RX + 2 * TY;
     static constexpr int RHO_BYTES = 2 * RX * RY * 4;
@@ -162,18 +168,22 @@ struct TmaTile {
     static constexpr int NSL = NS + 1;
     static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
     static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
-    // The tile's post-collision output, [22][TY][TX] (+ [3][TY][TX] FP16
-    // references), written by bulk tensor stores -- where it fits.
-    static constexpr int OUT_POP = NPOP * NT * (int)sizeof(T);
+    // The tile's post-collision output, [22][TY][TX] FP32 or [20][TY][TX]
+    // FP16 + [3][TY][TX] FP16 references + [2][TY][TX] FP32 rest planes,
+    // written by bulk tensor stores -- where it fits.
+    static constexpr int OUT_POP = NPL * NT * (int)sizeof(T);
+    static constexpr int OUT_REST = OUT_POP + (S::kHalf ? NMOM * NT * 2 : 0);
     static constexpr int OUT_BYTES =
-        (OUT_POP + (S::kHalf ? NMOM * NT * 2 : 0) + 127) / 128 * 128;
+        (OUT_REST + (S::kHalf ? NREST * NT * 4 : 0) + 127) / 128 * 128;
     static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
     static constexpr bool TS = OUT_OFF + OUT_BYTES + 128 <= 232448;
     static constexpr int BAR_OFF = OUT_OFF + (TS ? OUT_BYTES : 0);
     static constexpr int SMEM = BAR_OFF + 128;
     static_assert(SMEM <= 232448, "shared memory per block");
     static_assert((TX * (int)sizeof(T)) % 16 == 0, "store box row");
-    static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0, "stage alignment");
+    static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0 &&
+                      REST_OFF % 16 == 0 && OUT_REST % 16 == 0,
+                  "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static constexpr int RW = (NRING + NW - 1) / NW;  // ring cells per warp
     static_assert(NRING <= NT && RW <= 32, "ring spread");
@@ -182,20 +192,25 @@ struct TmaTile {
 
 // The 9 populations of component `comp` pulled into the node at stage cell
 // `c`, from shared memory (bb: bounce-back bits).  BB = false: no source is
-// solid, every address is the node's cell plus a constant.
+// solid, every address is the node's cell plus a constant.  FP16 storage:
+// deviations and references from the stage, the rest population (which
+// never moves) from the FP32 rest planes `rest`.
 template <class S, class TT, bool BB>
 __device__ __forceinline__ void spull9(const typename S::T *tile,
-                                       const __half *mom, int comp, int c,
-                                       unsigned bb, float f[Q]) {
+                                       const __half *mom, const float *rest,
+                                       int comp, int c, unsigned bb,
+                                       float f[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool b = BB && ((bb >> i) & 1u);
         const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
-        const int q = comp * Q + (b ? opp(i) : i);
+        const int qi = b ? opp(i) : i;
         if constexpr (!S::kHalf) {
-            f[i] = tile[q * TT::PL + cell];
+            f[i] = tile[(comp * Q + qi) * TT::PL + cell];
+        } else if (i == 0) {
+            f[0] = rest[comp * TT::PL + c];
         } else {
-            f[i] = dec_pop(b ? opp(i) : i, __half2float(tile[q * TT::PL + cell]),
+            f[i] = dec_pop(qi, __half2float(tile[sp16(comp * Q + qi) * TT::PL + cell]),
                            __half2float(mom[comp * TT::PL + cell]));
         }
     }
@@ -213,7 +228,7 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
         if constexpr (!S::kHalf) {
             g[k] = tile[q * TT::PL + cell];
         } else {
-            g[k] = dec_sol(__half2float(tile[q * TT::PL + cell]),
+            g[k] = dec_sol(__half2float(tile[sp16(q) * TT::PL + cell]),
                            __half2float(mom[2 * TT::PL + cell]));
         }
     }
@@ -222,15 +237,16 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
 // The 22 populations of the node at stage cell c.
 template <class S, class TT>
 __device__ __forceinline__ void spull22(const typename S::T *tile,
-                                        const __half *mom, int c, unsigned bb,
-                                        float fA[Q], float fB[Q], float g[QS]) {
+                                        const __half *mom, const float *rest,
+                                        int c, unsigned bb, float fA[Q],
+                                        float fB[Q], float g[QS]) {
     if (bb == 0u) {
-        spull9<S, TT, false>(tile, mom, 0, c, 0u, fA);
-        spull9<S, TT, false>(tile, mom, 1, c, 0u, fB);
+        spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, fA);
+        spull9<S, TT, false>(tile, mom, rest, 1, c, 0u, fB);
         spull4<S, TT, false>(tile, mom, c, 0u, g);
     } else {
-        spull9<S, TT, true>(tile, mom, 0, c, bb, fA);
-        spull9<S, TT, true>(tile, mom, 1, c, bb, fB);
+        spull9<S, TT, true>(tile, mom, rest, 0, c, bb, fA);
+        spull9<S, TT, true>(tile, mom, rest, 1, c, bb, fB);
         spull4<S, TT, true>(tile, mom, c, (bb >> 1) & 0xFu, g);
     }
 }
@@ -238,23 +254,24 @@ __device__ __forceinline__ void spull22(const typename S::T *tile,
 // Densities of both components at stage cell c.
 template <class S, class TT>
 __device__ __forceinline__ void sdens(const typename S::T *tile,
-                                      const __half *mom, int c, unsigned bb,
-                                      float &ra, float &rb) {
+                                      const __half *mom, const float *rest,
+                                      int c, unsigned bb, float &ra,
+                                      float &rb) {
     float f[Q];
     ra = 0.f;
     rb = 0.f;
     if (bb == 0u) {
-        spull9<S, TT, false>(tile, mom, 0, c, 0u, f);
+        spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) ra += f[i];
-        spull9<S, TT, false>(tile, mom, 1, c, 0u, f);
+        spull9<S, TT, false>(tile, mom, rest, 1, c, 0u, f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) rb += f[i];
     } else {
-        spull9<S, TT, true>(tile, mom, 0, c, bb, f);
+        spull9<S, TT, true>(tile, mom, rest, 0, c, bb, f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) ra += f[i];
-        spull9<S, TT, true>(tile, mom, 1, c, bb, f);
+        spull9<S, TT, true>(tile, mom, rest, 1, c, bb, f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) rb += f[i];
     }
@@ -292,21 +309,26 @@ __device__ __forceinline__ unsigned nb_bits(const uint8_t *sm, int mc,
     return r;
 }
 
+// Tensor maps of one launch, per lattice: the tile copies (populations,
+// FP16 references and FP32 rest planes, mask) and the output stores.
+struct TmaMaps {
+    const CUtensorMap *pop, *mom, *rest, *mask;
+    const CUtensorMap *out, *out_mom, *out_rest;
+};
+
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY)
-    k_step_tma(StepArgs a, const CUtensorMap *__restrict__ pop_maps,
-               const CUtensorMap *__restrict__ mom_maps,
-               const CUtensorMap *__restrict__ mask_maps,
-               const CUtensorMap *__restrict__ out_maps,
-               const CUtensorMap *__restrict__ out_mom_maps,
-               const TileRec *__restrict__ sched, int nslots,
-               int *__restrict__ err) {
+    k_step_tma(StepArgs a, TmaMaps mp, const TileRec *__restrict__ sched,
+               int nslots, int *__restrict__ err) {
     using TT = TmaTile<S, TX, TY>;
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem[];
     auto stage_pop = [&](int s) { return reinterpret_cast<T *>(smem + s * TT::STAGE); };
     auto stage_mom = [&](int s) {
         return reinterpret_cast<__half *>(smem + s * TT::STAGE + TT::POP_BYTES);
+    };
+    auto stage_rest = [&](int s) {
+        return reinterpret_cast<float *>(smem + s * TT::STAGE + TT::REST_OFF);
     };
     auto stage_mask = [&](int s) { return smem + s * TT::STAGE + TT::MASK_OFF; };
     auto sdesc = [&](int slot) {
@@ -341,10 +363,12 @@ __global__ void __launch_bounds__(TX *TY)
         fence_proxy_async();
         mbar_expect_tx(&bar[s], TT::TX_BYTES);
         bulk_load(sdesc(slot), a.desc + l, 128, &bar[s]);
-        tma_load_3d(stage_pop(s), &pop_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
-        if constexpr (S::kHalf)
-            tma_load_3d(stage_mom(s), &mom_maps[l], x0 - TT::XO, y0, 0, &bar[s]);
-        tma_load_2d(stage_mask(s), &mask_maps[l], x0 - TT::MXO, y0, &bar[s]);
+        tma_load_3d(stage_pop(s), &mp.pop[l], x0 - TT::XO, y0, 0, &bar[s]);
+        if constexpr (S::kHalf) {
+            tma_load_3d(stage_mom(s), &mp.mom[l], x0 - TT::XO, y0, 0, &bar[s]);
+            tma_load_3d(stage_rest(s), &mp.rest[l], x0 - TT::XO, y0, 0, &bar[s]);
+        }
+        tma_load_2d(stage_mask(s), &mp.mask[l], x0 - TT::MXO, y0, &bar[s]);
     };
 
     if (tid == 0) {
@@ -364,15 +388,19 @@ __global__ void __launch_bounds__(TX *TY)
     const MaskBits mb(t);
 
     // output tile in shared memory (TS): node lid = ly * TX + lx of plane q
-    // at sout[q * NT + lid]; FP16 references at smom_out[c * NT + lid]
+    // at sout[q * NT + lid]; FP16 references at smom_out[c * NT + lid], FP16
+    // rest populations at srest_out[c * NT + lid]
     T *sout = reinterpret_cast<T *>(smem + TT::OUT_OFF);
     __half *smom_out = reinterpret_cast<__half *>(smem + TT::OUT_OFF + TT::OUT_POP);
+    float *srest_out = reinterpret_cast<float *>(smem + TT::OUT_OFF + TT::OUT_REST);
     // bulk tensor store of the output tile (thread 0; every thread fenced
     // its writes and passed a barrier since)
     auto store_out = [&](const TileRec &r) {
-        tma_store_3d(&out_maps[r.lat], sout, r.x0, r.y0, 0);
-        if constexpr (S::kHalf)
-            tma_store_3d(&out_mom_maps[r.lat], smom_out, r.x0, r.y0, 0);
+        tma_store_3d(&mp.out[r.lat], sout, r.x0, r.y0, 0);
+        if constexpr (S::kHalf) {
+            tma_store_3d(&mp.out_mom[r.lat], smom_out, r.x0, r.y0, 0);
+            tma_store_3d(&mp.out_rest[r.lat], srest_out, r.x0, r.y0, 0);
+        }
         bulk_commit();
     };
     TileRec prev{-1, 0, 0, 0};  // thread 0: the tile whose output awaits its store
@@ -415,6 +443,7 @@ __global__ void __launch_bounds__(TX *TY)
         const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
         T *tp = stage_pop(s);
         __half *tm = stage_mom(s);
+        float *tr = stage_rest(s);
         uint8_t *sm = stage_mask(s);
 
         // own node: mask bits, pull, density
@@ -437,7 +466,7 @@ __global__ void __launch_bounds__(TX *TY)
         {
             float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
-                spull22<S, TT>(tp, tm, pc, bb, fA, fB, g);
+                spull22<S, TT>(tp, tm, tr, pc, bb, fA, fB, g);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
             }
@@ -461,7 +490,7 @@ __global__ void __launch_bounds__(TX *TY)
                 float ra = 0.f, rb = 0.f;
                 if (!(sm[rmc] & mb.force)) {
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
-                    sdens<S, TT>(tp, tm, rpc, rbb, ra, rb);
+                    sdens<S, TT>(tp, tm, tr, rpc, rbb, ra, rb);
                 }
                 fr[ry * TT::RX + rx] = ra;
                 fr[TT::RX * TT::RY + ry * TT::RX + rx] = rb;
@@ -509,7 +538,8 @@ __global__ void __launch_bounds__(TX *TY)
                     a, d, l, t, x, y, own, fA, fB, g, rAn, rBn, snb, ns,
                     [&](const float *pa, const float *pb, const float *pg) {
                         if (ts_tile)
-                            store_tile22<S, TT::NT>(sout + lid, smom_out + lid, pa, pb, pg);
+                            store_tile22<S, TT::NT>(sout + lid, smom_out + lid,
+                                                    srest_out + lid, pa, pb, pg);
                         else
                             store_node22<S>(a, d, own, pa, pb, pg);
                     });
@@ -549,17 +579,12 @@ static cudaError_t grid_tma_t(int *grid) {
 }
 
 template <class S, int TX, int TY>
-static cudaError_t launch_tma_t(const StepArgs &a, const CUtensorMap *pop_maps,
-                                const CUtensorMap *mom_maps,
-                                const CUtensorMap *mask_maps,
-                                const CUtensorMap *out_maps,
-                                const CUtensorMap *out_mom_maps,
+static cudaError_t launch_tma_t(const StepArgs &a, const TmaMaps &mp,
                                 const TileRec *sched, int nslots, int grid,
                                 int *err, cudaStream_t s) {
     using TT = TmaTile<S, TX, TY>;
-    k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(
-        a, pop_maps, mom_maps, mask_maps, out_maps, out_mom_maps, sched,
-        nslots, err);
+    k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(a, mp, sched, nslots,
+                                                          err);
     return cudaGetLastError();
 }
 
@@ -579,21 +604,21 @@ cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mom_maps,
+                            const CUtensorMap *rest_maps,
                             const CUtensorMap *mask_maps,
                             const CUtensorMap *out_maps,
                             const CUtensorMap *out_mom_maps,
+                            const CUtensorMap *out_rest_maps,
                             const TileRec *sched, int nslots, int grid, int tx,
                             int ty, bool half, int *err, cudaStream_t s) {
+    const TmaMaps mp{pop_maps, mom_maps, rest_maps, mask_maps,
+                     out_maps, out_mom_maps, out_rest_maps};
 #define LBM_TMA_CASE(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
-        return half ? launch_tma_t<Store16, X, Y>(a, pop_maps, mom_maps,     \
-                                                  mask_maps, out_maps,       \
-                                                  out_mom_maps, sched,       \
-                                                  nslots, grid, err, s)      \
-                    : launch_tma_t<Store32, X, Y>(a, pop_maps, mom_maps,     \
-                                                  mask_maps, out_maps,       \
-                                                  out_mom_maps, sched,       \
-                                                  nslots, grid, err, s);
+        return half ? launch_tma_t<Store16, X, Y>(a, mp, sched, nslots, grid, \
+                                                  err, s)                    \
+                    : launch_tma_t<Store32, X, Y>(a, mp, sched, nslots, grid, \
+                                                  err, s);
     LBM_TMA_SHAPES(LBM_TMA_CASE)
 #undef LBM_TMA_CASE
     return cudaErrorInvalidValue;

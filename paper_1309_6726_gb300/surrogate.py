@@ -18,7 +18,7 @@ mapped to g_ads by the calibrated table, tau_A / tau_B uniform on
 [0.6, 1.5]).
 
     python -m paper_1309_6726_gb300.surrogate [--train 4096] [--held-out 256]
-        [--length 1024] [--steps 20000] [--fit-steps 20000]
+        [--length 1024] [--steps 20000] [--ensemble 5] [--fit-steps 16000]
 
 prints one JSON line with the dataset cost, the fit and the judged errors.
 """
@@ -188,56 +188,77 @@ class FitLog:
 
 
 class Surrogate:
-    """The network (4 inputs, 3 x 256 tanh, 65 outputs) on the GPU."""
+    """An ensemble of networks (4 inputs, 3 x 256 tanh, 65 outputs) on the
+    GPU, each from its own initialisation and minibatch order; the
+    prediction is their mean."""
 
     def __init__(self, hidden: int = 256, layers: int = 3, seed: int = 0,
-                 max_batch: int = 8192):
+                 max_batch: int = 8192, members: int = 1):
         from . import mlp
-        self.net = mlp.Mlp(4, hidden, layers, N_TIMES + 1, max_batch)
-        rng = np.random.default_rng(seed)
-        ws, bs = [], []
-        for r, c in mlp.layer_shapes(4, hidden, layers, N_TIMES + 1):
-            lim = math.sqrt(6.0 / (r + c))  # Glorot uniform
-            ws.append(rng.uniform(-lim, lim, (r, c)))
-            bs.append(np.zeros(r))
-        self.net.set_params(mlp.pack(ws, bs))
+        self.nets = []
+        for k in range(members):
+            net = mlp.Mlp(4, hidden, layers, N_TIMES + 1, max_batch)
+            rng = np.random.default_rng([seed, k])
+            ws, bs = [], []
+            for r, c in mlp.layer_shapes(4, hidden, layers, N_TIMES + 1):
+                lim = math.sqrt(6.0 / (r + c))  # Glorot uniform
+                ws.append(rng.uniform(-lim, lim, (r, c)))
+                bs.append(np.zeros(r))
+            net.set_params(mlp.pack(ws, bs))
+            self.nets.append(net)
+
+    @property
+    def net(self):
+        return self.nets[0]
 
     def fit(self, x, y, steps: int = 20000, batch: int = 512,
             lr: float = 2e-3, lr_end: float = 1e-5, seed: int = 0) -> FitLog:
-        """Adam on minibatches with a cosine learning-rate decay."""
+        """Adam on minibatches with a cosine learning-rate decay, for each
+        member of the ensemble; the log reports the mean losses."""
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
         yd = torch.from_numpy(np.ascontiguousarray(y, np.float32)).to(dev)
         n = xd.shape[0]
         batch = min(batch, n)
-        g = torch.Generator(device="cpu").manual_seed(seed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        first = self.net.train_step(xd[:batch].contiguous(), yd[:batch].contiguous(),
-                                    lr, want_loss=True)
-        order = torch.randperm(n, generator=g).to(dev)
-        pos = 0
-        for k in range(1, steps):
-            if pos + batch > n:
-                order = torch.randperm(n, generator=g).to(dev)
-                pos = 0
-            idx = order[pos:pos + batch]
-            pos += batch
-            a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * k / steps))
-            self.net.train_step(xd.index_select(0, idx), yd.index_select(0, idx), a)
-        last = self.net.grad(xd, yd)[1] if n <= self.net.max_batch else float("nan")
+        firsts, lasts = [], []
+        for m, net in enumerate(self.nets):
+            g = torch.Generator(device="cpu").manual_seed(seed * 1000 + m)
+            firsts.append(net.train_step(xd[:batch].contiguous(),
+                                         yd[:batch].contiguous(), lr,
+                                         want_loss=True))
+            order = torch.randperm(n, generator=g).to(dev)
+            pos = 0
+            for k in range(1, steps):
+                if pos + batch > n:
+                    order = torch.randperm(n, generator=g).to(dev)
+                    pos = 0
+                idx = order[pos:pos + batch]
+                pos += batch
+                a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * k / steps))
+                net.train_step(xd.index_select(0, idx), yd.index_select(0, idx), a)
+            lasts.append(net.grad(xd, yd)[1] if n <= net.max_batch else float("nan"))
         torch.cuda.synchronize()
-        return FitLog(steps, time.perf_counter() - t0, first, last)
+        return FitLog(steps * len(self.nets), time.perf_counter() - t0,
+                      float(np.mean(firsts)), float(np.mean(lasts)))
 
     def predict(self, x) -> np.ndarray:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
-        return self.net.forward(xd).cpu().numpy()
+        out = self.nets[0].forward(xd)
+        for net in self.nets[1:]:
+            out += net.forward(xd)
+        return (out / len(self.nets)).cpu().numpy()
+
+    def params(self):
+        return [net.params() for net in self.nets]
 
     def close(self):
-        self.net.close()
+        for net in self.nets:
+            net.close()
 
 
 def predict_or_solve(model: Surrogate, members, t_grid, length: int):
@@ -262,12 +283,17 @@ def main(argv=None):
     ap.add_argument("--held-out", type=int, default=256)
     ap.add_argument("--length", type=int, default=1024)
     ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--fit-steps", type=int, default=40000)
+    ap.add_argument("--fit-steps", type=int, default=16000,
+                    help="Adam steps per ensemble member")
     ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--ensemble", type=int, default=5)
     ap.add_argument("--seed", type=int, default=1240)
     ap.add_argument("--save", default=None, help="write the weights (.npy)")
     ap.add_argument("--save-data", default=None,
                     help="write the trajectories (.npz)")
+    ap.add_argument("--data", default=None,
+                    help="read the trajectories (.npz from --save-data) "
+                         "instead of running the solver")
     args = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -276,14 +302,26 @@ def main(argv=None):
     grid = time_grid(args.steps)
     train_m = draw_members(args.train, args.seed, args.length)
     test_m = draw_members(args.held_out, args.seed + 1, args.length)
-    tr = run_trajectories(train_m, grid)
-    te = run_trajectories(test_m, grid)
+    if args.data:
+        dd = np.load(args.data)
+        tr = {"z": dd["z_train"], "closure": dd["c_train"],
+              "nonfinite": np.all(np.isnan(dd["z_train"]), axis=1),
+              "seconds": float("nan"), "fluid_nodes": 0, "steps": args.steps}
+        te = {"z": dd["z_test"], "closure": dd["c_test"],
+              "nonfinite": np.all(np.isnan(dd["z_test"]), axis=1),
+              "seconds": float("nan"), "fluid_nodes": 0, "steps": args.steps}
+        if not (np.array_equal(dd["x_train"], features(train_m)) and
+                np.array_equal(dd["times"], grid)):
+            raise SystemExit("--data was written for other parameters")
+    else:
+        tr = run_trajectories(train_m, grid)
+        te = run_trajectories(test_m, grid)
     x, y = features(train_m), targets(tr["z"], tr["closure"], args.steps)
     if args.save_data:
         np.savez(args.save_data, x_train=x, z_train=tr["z"],
                  c_train=tr["closure"], x_test=features(test_m),
                  z_test=te["z"], c_test=te["closure"], times=grid)
-    model = Surrogate(seed=args.seed)
+    model = Surrogate(seed=args.seed, members=args.ensemble)
     log = model.fit(x, y, steps=args.fit_steps, batch=args.batch)
     xt = features(test_m)
     model.predict(xt)  # warm-up
@@ -294,7 +332,7 @@ def main(argv=None):
     zp, cp = decode(yp, args.steps)
     res = judge(zp, cp, te["z"], te["closure"], args.steps)
     if args.save:
-        np.save(args.save, model.net.params())
+        np.save(args.save, np.stack(model.params()))
     out = {
         "length": args.length, "steps": args.steps, "times": len(grid),
         "train_runs": args.train, "held_out_runs": args.held_out,
@@ -302,8 +340,10 @@ def main(argv=None):
         "held_out_nonfinite": int(te["nonfinite"].sum()),
         "solver_seconds_train": tr["seconds"],
         "solver_seconds_held_out": te["seconds"],
-        "solver_glups_held_out": te["fluid_nodes"] * te["steps"] / te["seconds"] / 1e9,
-        "fit": {"steps": log.steps, "seconds": log.seconds,
+        "solver_glups_held_out": (te["fluid_nodes"] * te["steps"] / te["seconds"] / 1e9
+                                  if te["fluid_nodes"] else None),
+        "fit": {"ensemble": args.ensemble, "steps": log.steps,
+                "seconds": log.seconds,
                 "first_loss": log.first_loss, "last_loss": log.last_loss},
         "network_seconds_held_out": t_net,
         "speedup_vs_solver": te["seconds"] / max(t_net, 1e-9),
