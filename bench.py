@@ -38,8 +38,9 @@ METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated err
 #: algorithmic bytes per fluid-node update of the step kernel: each stored
 #: element read once and written once, the mask byte read once.
 #: FP32: 22 populations x 4 B x 2 = 176, + 1 mask byte.
-#: FP16: 22 deviations x 2 B x 2 = 88, 3 moment values x 2 B x 2 = 12, + 1.
-BYTES_PER_NODE = {"fp32": 177.0, "fp16": 101.0}
+#: FP16: 20 deviations x 2 B x 2 = 80, 3 references x 2 B x 2 = 12,
+#: 2 FP32 rest populations x 4 B x 2 = 16, + 1.
+BYTES_PER_NODE = {"fp32": 177.0, "fp16": 109.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel
@@ -48,7 +49,7 @@ DEPOSIT_BYTES = 16.0
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.57, "fp16": 105.75}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 114.88}
 
 
 def load_peaks():
@@ -358,8 +359,10 @@ def main():
                                            / 1e9) / g2}
     peak, peak_kind = load_peaks()
     traffic = None
-    if args.workload == "sweep" and not os.environ.get("LBM_TILE"):
-        traffic = TRAFFIC_PER_FLUID_NODE[args.precision] * n_fluid
+    per_node = TRAFFIC_PER_FLUID_NODE[args.precision]
+    if (args.workload == "sweep" and not os.environ.get("LBM_TILE")
+            and per_node is not None):
+        traffic = per_node * n_fluid
     bpn = BYTES_PER_NODE[args.precision] + DEPOSIT_BYTES * f_s
     achieved = n_fluid * bpn / (ms_step / 1e3) / 1e9
     e2e = None
