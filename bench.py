@@ -44,12 +44,12 @@ BYTES_PER_NODE = {"fp32": 177.0, "fp16": 109.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel
-#: (default 64 x 8 tiles), from one ncu capture (dram__bytes_read.sum +
+#: (default tiles: 64 x 8 FP32, 64 x 4 FP16), from one ncu capture (dram__bytes_read.sum +
 #: dram__bytes_write.sum) of the first 40 capillaries of the sweep -- the
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 114.88}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 117.15}
 
 
 def load_peaks():

@@ -65,9 +65,8 @@ static_assert(sizeof(lbm_obs) == 8 * 16 + 4 * 2 + 8, "lbm_obs layout");
 struct lbm_handle {
     int count = 0;
     bool half = false;
-    // tile of the step kernel: 64 x 8 measured fastest on the batched sweep
-    // in both storage precisions (LBM_TILE overrides, lbm_autotune picks
-    // per workload)
+    // tile of the step kernel (LBM_TILE overrides, lbm_autotune picks per
+    // workload); set by pick_tile
     int tx = 64, ty = 8;
     bool use_tma = true;
     std::vector<LatDesc> desc;
@@ -182,6 +181,11 @@ static bool valid_params(const lbm_params &p, std::string &why) {
 }
 
 static void pick_tile(lbm_handle *h) {
+    // measured fastest on the batched sweep: 64 x 8 for FP32 storage (one
+    // 512-thread block per SM), 64 x 4 for FP16 (its smaller tiles fit two
+    // 256-thread blocks per SM, which hides the issue-bound codec better)
+    h->tx = 64;
+    h->ty = h->half ? 4 : 8;
     const char *e = getenv("LBM_TILE");
     if (e) {
         int a = 0, b = 0;
