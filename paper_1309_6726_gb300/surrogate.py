@@ -6,7 +6,8 @@ tau_A / tau_B -- to its infiltration curve, the front position z at 64
 log-spaced times, and to its pore-closure time.  It is trained on
 trajectories that the batched lattice Boltzmann solver generates (all
 members of a training set advance together in one persistent launch per
-step), and the solver stays the judge of its error on held-out parameters
+step), and the solver stays the reference its error is measured against on
+held-out parameters
 and the fallback for parameters outside the training domain.
 
 Capillary length, reservoirs and the horizon are fixed for a surrogate
@@ -20,7 +21,8 @@ mapped to g_ads by the calibrated table, tau_A / tau_B uniform on
     python -m paper_1309_6726_gb300.surrogate [--train 4096] [--held-out 256]
         [--length 1024] [--steps 20000] [--ensemble 5] [--fit-steps 16000]
 
-prints one JSON line with the dataset cost, the fit and the judged errors.
+prints one JSON line with the dataset cost, the fit and the errors against
+the solver.
 """
 from __future__ import annotations
 
@@ -128,7 +130,8 @@ def _log_tmax(t_max):
 def targets(z, closure, t_max) -> np.ndarray:
     """Network targets: asinh(z / Z_SCALE) at each time (close to the
     relative error for fronts beyond Z_SCALE, the absolute one below it:
-    the judge's measure), then the closure time as log10(t) / log10(t_max),
+    the error measure of compare_to_solver), then the closure time as
+    log10(t) / log10(t_max),
     or (log10(t_max) + 0.3) / log10(t_max) when the run did not close
     within t_max.  NaN marks what is unknown."""
     lt = _log_tmax(t_max)
@@ -150,7 +153,7 @@ def decode(y, t_max):
     return z, closure.astype(np.int64)
 
 
-def judge(z_pred, c_pred, z_lb, c_lb, t_max):
+def compare_to_solver(z_pred, c_pred, z_lb, c_lb, t_max):
     """Errors of the surrogate against the solver on the same runs.
 
     Front: per run, the mean over the times of |z_pred - z_lb| divided by
@@ -330,7 +333,7 @@ def main(argv=None):
     yp = model.predict(xt)
     t_net = time.perf_counter() - t0
     zp, cp = decode(yp, args.steps)
-    res = judge(zp, cp, te["z"], te["closure"], args.steps)
+    res = compare_to_solver(zp, cp, te["z"], te["closure"], args.steps)
     if args.save:
         np.save(args.save, np.stack(model.params()))
     out = {
@@ -347,7 +350,7 @@ def main(argv=None):
                 "first_loss": log.first_loss, "last_loss": log.last_loss},
         "network_seconds_held_out": t_net,
         "speedup_vs_solver": te["seconds"] / max(t_net, 1e-9),
-        "judge": res,
+        "vs_solver": res,
     }
     print(json.dumps(out))
     model.close()

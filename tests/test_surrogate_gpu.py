@@ -1,5 +1,5 @@
 """The surrogate end to end at a small scale: trajectories from the batched
-solver, training with the library's kernels, the solver as judge on
+solver, training with the library's kernels, the solver as the reference on
 held-out parameters, the solver as fallback outside the training domain,
 and what the network gains over running the solver."""
 import time
@@ -39,7 +39,7 @@ def test_surrogate_learns_solver_trajectories_and_saves_time():
     yp = model.predict(xt)
     t_net = time.perf_counter() - t0
     zp, cp = S.decode(yp, steps)
-    res = S.judge(zp, cp, te["z"], te["closure"], steps)
+    res = S.compare_to_solver(zp, cp, te["z"], te["closure"], steps)
     print(res, "solver %.3f s, network %.5f s" % (te["seconds"], t_net))
     # a small training set at a short horizon: a looser bound than the
     # 2 percent of the full-size run, but well below an untrained guess
