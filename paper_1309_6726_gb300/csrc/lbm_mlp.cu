@@ -21,6 +21,7 @@ namespace lbmmlp {
 
 constexpr int BM = 64, BN = 64, BK = 32, KP = BK + 8;  // KP: padded row
 constexpr int GEMM_THREADS = 128;                        // 2 x 2 warps
+constexpr int kSplit = 8;  // K split of the weight-gradient products
 
 enum Epi : int {
     EPI_PLAIN = 0,      // C = A B
@@ -52,14 +53,16 @@ __device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4],
 
 // C[m][n] (row stride ldc) = epilogue(sum_k A(m, k) B(k, n)), m < M, n < N,
 // with A(m, k) = a[m * sam + k * sak] and B(k, n) = b[k * sbk + n * sbn],
-// both rounded to BF16 on their way into shared memory.
+// both rounded to BF16 on their way into shared memory.  Split K
+// (EPI_PLAIN only): block z sums k in [z kchunk, (z + 1) kchunk) and writes
+// its partial product to c + z * M * ldc (k_sum_parts adds them up).
 template <class TA, class TB>
 __global__ void __launch_bounds__(GEMM_THREADS)
     gemm_bf16(int M, int N, int K, const TA *__restrict__ a, long sam,
               long sak, const TB *__restrict__ b, long sbk, long sbn,
               float *__restrict__ c, long ldc, int epi,
               const float *__restrict__ bias, const float *__restrict__ h,
-              long ldh) {
+              long ldh, int kchunk) {
     __shared__ __align__(16) __nv_bfloat16 As[BM][KP];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][KP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -68,7 +71,10 @@ __global__ void __launch_bounds__(GEMM_THREADS)
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
     float acc[2][4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(K, kb + kchunk);
+    c += (long)blockIdx.z * M * ldc;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
         // A tile, BM x BK: walk the unit-stride index fastest
         if (sak == 1) {
 #pragma unroll 2
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 const int e = tid + j * GEMM_THREADS;
                 const int kk = e % BK, mm = e / BK;
                 const int m = m0 + mm, k = k0 + kk;
-                As[mm][kk] = (m < M && k < K) ? to_bf16(a[m * sam + k]) : zero;
+                As[mm][kk] = (m < M && k < ke) ? to_bf16(a[m * sam + k]) : zero;
             }
         } else {
 #pragma unroll 2
@@ -84,7 +90,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 const int e = tid + j * GEMM_THREADS;
                 const int mm = e % BM, kk = e / BM;
                 const int m = m0 + mm, k = k0 + kk;
-                As[mm][kk] = (m < M && k < K) ? to_bf16(a[m * sam + k * sak]) : zero;
+                As[mm][kk] = (m < M && k < ke) ? to_bf16(a[m * sam + k * sak]) : zero;
             }
         }
         // B tile, BK x BN, kept n-major: Bs[n][k]
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 const int e = tid + j * GEMM_THREADS;
                 const int nn = e % BN, kk = e / BN;
                 const int n = n0 + nn, k = k0 + kk;
-                Bs[nn][kk] = (n < N && k < K) ? to_bf16(b[k * sbk + n]) : zero;
+                Bs[nn][kk] = (n < N && k < ke) ? to_bf16(b[k * sbk + n]) : zero;
             }
         } else {
 #pragma unroll 2
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 const int e = tid + j * GEMM_THREADS;
                 const int kk = e % BK, nn = e / BK;
                 const int n = n0 + nn, k = k0 + kk;
-                Bs[nn][kk] = (n < N && k < K) ? to_bf16(b[k * sbk + n * sbn]) : zero;
+                Bs[nn][kk] = (n < N && k < ke) ? to_bf16(b[k * sbk + n * sbn]) : zero;
             }
         }
         __syncthreads();
@@ -148,6 +154,17 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 }
                 c[m * ldc + n] = v;
             }
+}
+
+// c[i] = sum over z of parts[z * n + i], in order z = 0, 1, ...
+__global__ void k_sum_parts(const float *__restrict__ parts, int nparts,
+                            long n, float *__restrict__ c) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < nparts; ++z) v += parts[z * n + i];
+        c[i] = v;
+    }
 }
 
 // dy = 2 (y - t) / (rows * cols) where t is a number, 0 where t is NaN;
@@ -224,6 +241,7 @@ struct lbm_mlp {
     __nv_bfloat16 *wb = nullptr;
     std::vector<float *> hs;         // hidden activations, [max_batch][H]
     float *y = nullptr, *dy = nullptr, *dz[2] = {nullptr, nullptr};
+    float *split = nullptr;  // split-K partial products of a weight gradient
     double *d_loss = nullptr;
     cudaStream_t own = nullptr, stream = nullptr;
     long adam_t = 0;
@@ -260,7 +278,29 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA *a, long sam,
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     gemm_bf16<TA, TB><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, a, sam, sak, b,
                                                     sbk, sbn, c, ldc, epi,
-                                                    bias, hh, ldh);
+                                                    bias, hh, ldh, K);
+    return cudaGetLastError();
+}
+
+// C = A B (M x N, row stride N) with K split over `parts` blocks of
+// columns-of-work when the plain grid is small; the partial products go to
+// `scratch` (parts * M * N floats) and are added in a fixed order.
+template <class TA, class TB>
+cudaError_t gemm_split(cudaStream_t s, int M, int N, int K, const TA *a,
+                       long sam, long sak, const TB *b, long sbk, long sbn,
+                       float *c, float *scratch, int parts) {
+    const int kchunk = ((K + parts - 1) / parts + BK - 1) / BK * BK;
+    parts = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, parts);
+    gemm_bf16<TA, TB><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, a, sam, sak, b,
+                                                    sbk, sbn, scratch, (long)N,
+                                                    EPI_PLAIN, nullptr, nullptr,
+                                                    0, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long n = (long)M * N;
+    k_sum_parts<<<(int)std::min<long>((n + 255) / 256, 1024), 256, 0, s>>>(
+        scratch, parts, n, c);
     return cudaGetLastError();
 }
 
@@ -294,9 +334,10 @@ cudaError_t backward(lbm_mlp *h, const float *x, int batch) {
     for (int l = L; l >= 0 && e == cudaSuccess; --l) {
         const int K = in_of(h, l), N = out_of(h, l);
         const float *in = l == 0 ? x : h->hs[l - 1];
-        // dW_l[n][k] = sum_b dz[b][n] in[b][k]
-        e = gemm(h->stream, N, K, batch, dzl, 1L, (long)N, in, (long)K, 1L,
-                 h->grad + h->off_w[l], (long)K, EPI_PLAIN);
+        // dW_l[n][k] = sum_b dz[b][n] in[b][k]: a small output and a long
+        // sum over the batch, split into kSplit parts
+        e = gemm_split(h->stream, N, K, batch, dzl, 1L, (long)N, in, (long)K,
+                       1L, h->grad + h->off_w[l], h->split, kSplit);
         if (e != cudaSuccess) break;
         k_colsum<<<(N + 127) / 128, 128, 0, h->stream>>>(dzl, batch, N,
                                                          h->grad + h->off_b[l]);
@@ -378,6 +419,12 @@ lbm_status lbm_mlp_create(const lbm_mlp_shape *shape, lbm_mlp **out) {
     al(&h->dz[0], (size_t)s.max_batch * s.n_hidden);
     al(&h->dz[1], (size_t)s.max_batch * s.n_hidden);
     al(&h->d_loss, 1);
+    {
+        long wmax = 0;  // largest weight matrix
+        for (int l = 0; l <= s.n_layers; ++l)
+            wmax = std::max(wmax, (long)out_of(h, l) * in_of(h, l));
+        al(&h->split, (size_t)kSplit * wmax);
+    }
     if (ok && cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess)
         ok = false;
     h->stream = h->own;
@@ -473,7 +520,8 @@ void lbm_mlp_destroy(lbm_mlp *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void *p : {(void *)h->w, (void *)h->grad, (void *)h->m1, (void *)h->m2,
                     (void *)h->wb, (void *)h->y, (void *)h->dy,
-                    (void *)h->dz[0], (void *)h->dz[1], (void *)h->d_loss})
+                    (void *)h->dz[0], (void *)h->dz[1], (void *)h->d_loss,
+                    (void *)h->split})
         if (p) cudaFree(p);
     for (float *p : h->hs)
         if (p) cudaFree(p);
