@@ -132,14 +132,17 @@ def test_batch_matches_independent_lattices():
         assert obs[k]["delta_e"] == oo["delta_e"]
 
 
-def test_checkpoint_continues_bit_for_bit(tmp_path):
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_checkpoint_continues_bit_for_bit(tmp_path, precision):
+    # FP16 checkpoints carry the deviations, the FP16 references and the
+    # FP32 rest planes
     geom, mp, _ = I.config_small()
-    a = lbm.Solver(geom, mp)
+    a = lbm.Solver(geom, mp, precision)
     a.step(700)
     path = str(tmp_path / "ck.bin")
     a.save(path)
     a.step(300)
-    b = lbm.Solver(geom, mp)
+    b = lbm.Solver(geom, mp, precision)
     b.load(path)
     assert b.step_count == 700
     b.step(300)
