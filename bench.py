@@ -261,7 +261,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    geoms, params, desc = build_workload(args.workload)
+    geoms, params, desc = build_workload(args.workload, 0, args.lattices)
     times = []
     from oracle.lattice import Lattice, Params
     sizes = np.array([g.solid.size for g in geoms])
@@ -287,7 +287,10 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc},
+        "config": {"workload": desc, "lattices": len(geoms),
+                   "fluid_nodes": fluid_nodes(geoms),
+                   "all_nodes": all_nodes(geoms),
+                   "parallelism": "host oracle, one capillary per step"},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
