@@ -248,19 +248,41 @@ __global__ void k_mask_agree(const LatDesc *desc, int l, uint8_t *mask_all,
 }
 
 // ---------------------------------------------------------------------------
-// Observables.  Pass 1: blocks of 32 x 8 threads take 32 consecutive columns
-// of all lattices (numbered through col_base): lane = column, so loads
-// coalesce along rows, and the 8 warps split the rows of each column
-// (y = warp, warp + 8, ...); their partial results meet in shared memory
-// and are combined in a fixed order into one ColObs per column.
+// Observables.  Pass 1: blocks of 32 x OBS_ROWS threads take 32 consecutive
+// columns of all lattices (numbered through col_base): lane = column, so
+// loads coalesce along rows, and the warps split the rows of each column.
+//
+// Masses need no pull: streaming with bounce-back hands every stored value
+// of a node that was fluid in the last step to exactly one node that was
+// fluid then, so the stored values of those nodes sum to the post-streaming
+// content of the fluid nodes plus that of the nodes turned solid at the end
+// of the last step (the pending ones, pulled separately, which go to the
+// ledger).  Only the nodes whose phase the observables need -- the lowest
+// and highest fluid row of a column, and the centreline rows -- are pulled,
+// once the partial results have met in shared memory.
 // Pass 2: one block per lattice reduces the columns.
 // ---------------------------------------------------------------------------
 
 struct ObsPart {
-    double mass[4], pend[4];
-    float phi0, phi1;
-    int h, fl0, fl1, nonfin, klo, khi;
+    double stored[3], pend[4], dep;
+    int h, nonfin, lo, hi;
 };
+
+// Sum of the 22 stored values of a node (A, B, solute), as readers decode
+// them.
+__device__ __forceinline__ void stored_sums(const void *fin, const __half *mom,
+                                            const LatDesc &d, bool half,
+                                            int64_t own, float &sa, float &sb,
+                                            float &sc) {
+    sa = 0.f;
+    sb = 0.f;
+    sc = 0.f;
+    for (int i = 0; i < Q; ++i) {
+        sa += load_pop(fin, mom, d, half, i, own);
+        sb += load_pop(fin, mom, d, half, Q + i, own);
+    }
+    for (int k = 0; k < QS; ++k) sc += load_pop(fin, mom, d, half, 2 * Q + k, own);
+}
 
 __global__ void __launch_bounds__(32 * OBS_ROWS)
     k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
@@ -270,24 +292,30 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
     __shared__ ObsPart part[OBS_ROWS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int c = blockIdx.x * 32 + lane;
+    const MaskBits mb(t);
     ObsPart p = {};
-    p.klo = 0x7fffffff;  // lowest / highest fluid row: key = 2 y + phase
-    p.khi = -1;
-    int ny = 0;
+    p.lo = 0x7fffffff;  // lowest / highest fluid row of the column
+    p.hi = -1;
     if (c < ncols_total) {
         const int l = col_lat[c];
         const LatDesc d = desc[l];
         const int x = (int)(c - col_base[l]);
-        const MaskBits mb(t);
         const uint8_t *mask = mask_all + d.node_off;
-        ny = d.ny;
-        const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
         float v[NPOP];
-        for (int y = w; y < ny; y += OBS_ROWS) {
+        for (int y = w; y < d.ny; y += OBS_ROWS) {
             const int64_t own = (int64_t)y * d.pitch + x;
-            const uint8_t s = mask[own];
-            if (s & mb.force) {
-                if (!(s & mb.pull)) {  // turned solid at the end of the last step
+            const uint8_t sv = mask[own];
+            const bool fluid_before = !(sv & mb.pull);
+            if (fluid_before) {
+                float sa, sb, sc;
+                stored_sums(fin, min_, d, half, own, sa, sb, sc);
+                if (!(sa + sb < 3.0e38f)) p.nonfin = 1;
+                p.stored[0] += sa;
+                p.stored[1] += sb;
+                p.stored[2] += sc;
+            }
+            if (sv & mb.force) {
+                if (fluid_before) {  // turned solid at the end of the last step
                     pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
                     double ra = 0, rb = 0;
                     for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
@@ -298,57 +326,68 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
                 }
                 continue;
             }
-            pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
-            float ra = 0.f, rb = 0.f;
-            for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
-            const float cc = v[18] + v[19] + v[20] + v[21];
-            if (!(ra + rb < 3.0e38f)) p.nonfin = 1;
-            p.mass[0] += ra;
-            p.mass[1] += rb;
-            p.mass[2] += cc;
-            p.mass[3] += m_all[d.node_off + own];
+            p.dep += m_all[d.node_off + own];
             p.h += 1;
-            const int key = 2 * y + (ra > rb ? 1 : 0);
-            p.klo = min(p.klo, key);
-            p.khi = max(p.khi, key);
-            if (y == yc0) { p.phi0 = ra - rb; p.fl0 = 1; }
-            if (y == yc1) { p.phi1 = ra - rb; p.fl1 = 1; }
+            p.lo = min(p.lo, y);
+            p.hi = max(p.hi, y);
         }
     }
     part[w][lane] = p;
     __syncthreads();
     if (w != 0 || c >= ncols_total) return;
+    double st[3] = {0, 0, 0};
     ColObs o = {};
-    int klo = 0x7fffffff, khi = -1;
-    for (int k = 0; k < OBS_ROWS; ++k) {
+    int lo = 0x7fffffff, hi = -1;
+    for (int k = 0; k < OBS_ROWS; ++k) {  // fixed order
         const ObsPart &q = part[k][lane];
-        o.mass_a += q.mass[0];
-        o.mass_b += q.mass[1];
-        o.mass_c += q.mass[2];
-        o.mass_m += q.mass[3];
+        for (int j = 0; j < 3; ++j) st[j] += q.stored[j];
         o.pend_a += q.pend[0];
         o.pend_b += q.pend[1];
         o.pend_c += q.pend[2];
         o.pend_m += q.pend[3];
-        if (q.fl0) { o.phi0 = q.phi0; o.fl0 = 1; }
-        if (q.fl1) { o.phi1 = q.phi1; o.fl1 = 1; }
+        o.mass_m += q.dep;
         o.h += q.h;
         o.nonfinite |= q.nonfin;
-        klo = min(klo, q.klo);
-        khi = max(khi, q.khi);
+        lo = min(lo, q.lo);
+        hi = max(hi, q.hi);
     }
+    // fluid content: stored content of the nodes fluid in the last step,
+    // less what the pending ones received (totals over a lattice are exact;
+    // a single column's share is not, streaming crosses columns)
+    o.mass_a = st[0] - o.pend_a;
+    o.mass_b = st[1] - o.pend_b;
+    o.mass_c = st[2] - o.pend_c;
+    const int l = col_lat[c];
+    const LatDesc d = desc[l];
+    const int x = (int)(c - col_base[l]);
+    const uint8_t *mask = mask_all + d.node_off;
+    const int ny = d.ny;
+    float v[NPOP];
+    // rho_A - rho_B of fluid node (x, y), pulled
+    auto phi = [&](int y) {
+        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        float ra = 0.f, rb = 0.f;
+        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+        return ra - rb;
+    };
+    auto fluid_now = [&](int y) {
+        return !(mask[(int64_t)y * d.pitch + x] & mb.force);
+    };
     if (o.h == 0) {
         o.b = ny;
         o.t = ny;
         o.wet_lo = o.wet_hi = 0;
     } else {
         // the walls are the solid runs below the lowest and above the
-        // highest fluid row
-        o.b = klo >> 1;
-        o.t = ny - 1 - (khi >> 1);
-        o.wet_lo = klo & 1;
-        o.wet_hi = khi & 1;
+        // highest fluid row; the wetting phase is read at those rows
+        o.b = lo;
+        o.t = ny - 1 - hi;
+        o.wet_lo = phi(lo) > 0.f;
+        o.wet_hi = hi == lo ? o.wet_lo : phi(hi) > 0.f;
     }
+    const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
+    if (fluid_now(yc0)) { o.phi0 = phi(yc0); o.fl0 = 1; }
+    if (fluid_now(yc1)) { o.phi1 = yc1 == yc0 ? o.phi0 : phi(yc1); o.fl1 = 1; }
     out[c] = o;
 }
 
