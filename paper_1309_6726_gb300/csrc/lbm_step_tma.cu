@@ -4,16 +4,19 @@
 //
 //   * the kernel is persistent: a grid of (SM count x resident blocks)
 //     walks the tiles of every lattice of the batch;
-//   * for each tile of TX x TY nodes, one thread issues a single 3-D bulk
-//     tensor copy (cp.async.bulk.tensor) of all 22 population planes over
-//     the tile plus a halo of 2 rows and 4 (FP32) or 8 (FP16) columns --
-//     the x start stays 16-byte aligned -- into shared memory, completing
-//     on an mbarrier; FP16 storage adds a second copy of the 3 moment
-//     planes;
-//   * three stages where they fit in shared memory (else two): the copies
-//     of the next tiles are in flight while the current one is computed;
+//   * for each tile of TX x TY nodes, one thread issues a 3-D bulk tensor
+//     copy (cp.async.bulk.tensor) of the population planes over the tile
+//     plus a halo of 2 rows and 4 (FP32) or 8 (FP16) columns -- the x start
+//     stays 16-byte aligned -- into shared memory, completing on an
+//     mbarrier; FP16 storage adds copies of the 3 reference planes and the
+//     2 FP32 rest planes; the mask box and the lattice descriptor come
+//     with them;
+//   * two stages: the copy of the next tile is in flight while the current
+//     one is computed;
 //   * all pulls -- the tile's own nodes and the one-node density ring the
 //     cohesion stencil needs -- then read shared memory at fixed offsets;
+//   * the tile's post-collision values go to a shared output tile that one
+//     bulk tensor store per tile (and plane group) copies out;
 //   * the lattice planes carry a two-node periodic ghost band (rows and
 //     columns), so every copy reads valid neighbours and nothing needs
 //     patching;
