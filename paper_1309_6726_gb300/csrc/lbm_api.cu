@@ -105,6 +105,7 @@ struct lbm_handle {
     int sched_grid = 0, sched_slots = 0;
     cudaGraphExec_t graph = nullptr;   // kGraphSteps steps from cur == 0
     bool use_graph = true;
+    int stall_tx = 0;  // test hook, see pick_tile
     int *d_err = nullptr;              // kernel error flags
     int cur = 0;
     int64_t steps = 0;
@@ -198,6 +199,11 @@ static void pick_tile(lbm_handle *h) {
     if (k && strcmp(k, "direct") == 0) h->use_tma = false;
     const char *gr = getenv("LBM_GRAPH");
     if (gr && strcmp(gr, "0") == 0) h->use_graph = false;
+    // test hook of the failure path: the first step's first tile of block 0
+    // waits for bytes that never arrive (the bounded wait runs out and the
+    // step reports LBM_ETIMEOUT); never set in normal use
+    const char *st = getenv("LBM_TEST_STALL");
+    if (st) h->stall_tx = std::min(std::max(atoi(st), 0), 1 << 20);
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -713,6 +719,7 @@ static StepArgs step_args(lbm_handle *h) {
     a.st = h->d_st;
     a.step = h->d_step;
     a.done = h->d_done;
+    a.stall_tx = h->stall_tx;
     return a;
 }
 
@@ -765,7 +772,9 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     // whole groups of kGraphSteps steps replay one captured graph (the
     // step count lives on the device, so the graph needs no new arguments)
-    while (h->use_graph && n >= kGraphSteps + (h->cur ? 1 : 0)) {
+    // (a pending test stall is never captured into the graph)
+    while (h->use_graph && h->stall_tx == 0 &&
+           n >= kGraphSteps + (h->cur ? 1 : 0)) {
         if (h->cur) {  // one plain step to get back to buffer 0
             CK(h, launch_one(h));
             h->cur ^= 1;
@@ -789,6 +798,7 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
         if (e == cudaErrorInvalidValue && k == 0)
             return fail(h, LBM_EINVAL, "unsupported tile shape");
         CK(h, e);
+        h->stall_tx = 0;  // the test stall applies to one launch
         h->cur ^= 1;
         h->steps += 1;
     }

@@ -141,6 +141,9 @@ struct StepArgs {
     LatState *st;
     int64_t *step;          // completed steps (read at start, bumped at end)
     unsigned int *done;     // blocks finished in this launch
+    // test hook of the bounded waits: bytes that block 0 expects on top of
+    // its first tile's copies and that no copy delivers (0 normally)
+    int32_t stall_tx;
 };
 
 constexpr int GHOST = 2;  // ghost rows on each side in y

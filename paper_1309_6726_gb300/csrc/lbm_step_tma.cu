@@ -358,13 +358,13 @@ __global__ void __launch_bounds__(TX *TY)
     const int lane = tid & 31, warp = tid >> 5;
 
     // Copies tile r into stage s and its lattice descriptor into `slot`.
-    auto issue = [&](const TileRec &r, int s, int slot) {
+    auto issue = [&](const TileRec &r, int s, int slot, int extra_tx) {
         const int l = r.lat;
         // physical coordinates: column x0 - XO and row y0 - 2 of the lattice
         const int x0 = r.x0 + XGHOST;
         const int y0 = r.y0;
         fence_proxy_async();
-        mbar_expect_tx(&bar[s], TT::TX_BYTES);
+        mbar_expect_tx(&bar[s], TT::TX_BYTES + extra_tx);
         bulk_load(sdesc(slot), a.desc + l, 128, &bar[s]);
         tma_load_3d(stage_pop(s), &mp.pop[l], x0 - TT::XO, y0, 0, &bar[s]);
         if constexpr (S::kHalf) {
@@ -383,7 +383,9 @@ __global__ void __launch_bounds__(TX *TY)
             const TileRec r = more && j < NS ? sched_at(j) : TileRec{-1, 0, 0, 0};
             s_rec[j] = r;
             more = r.lat >= 0;
-            if (more) issue(r, j, j);
+            // (the test hook: block 0's first tile waits for bytes that
+            // never come, so its bounded wait runs out)
+            if (more) issue(r, j, j, j == 0 && blockIdx.x == 0 ? a.stall_tx : 0);
         }
     }
     __syncthreads();
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(TX *TY)
         // stage s is free: start the copy of the tile NS ahead into it
         if (tid == 0) {
             s_rec[(k + NS) % NSL] = nxt;
-            if (nxt.lat >= 0) issue(nxt, s, (k + NS) % NSL);
+            if (nxt.lat >= 0) issue(nxt, s, (k + NS) % NSL, 0);
         }
 
         if (active) {
