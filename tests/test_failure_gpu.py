@@ -46,3 +46,31 @@ def test_bounded_wait_times_out_with_a_status(monkeypatch):
     np.testing.assert_array_equal(s2.solid_mask(), o.solid())
     assert pop_error(s2.populations(), oracle_pops(o)) < 1e-5
     s2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_non_finite_lattice_is_flagged_alone(precision):
+    # A batch of two capillaries; one gets a NaN population (a blown-up
+    # state).  Observables report LBM_ENAN, flag that lattice only, and the
+    # other lattice goes on exactly as it would alone.
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_6726_gb300 import inputs as I, lbm
+
+    geom = I.capillary(96, 14, 24, 16)
+    mp = I.ModelParams(g_ads=I.G_ADS_30, k_r=1e-3, inlet=1)
+    s = lbm.Solver([geom, geom], [mp, mp], precision)
+    alone = lbm.Solver(geom, mp, precision)
+    bad = s.populations(1)
+    bad[3, 7, 50] = np.nan
+    s.set_populations(bad, 1)
+    s.step(20)
+    alone.step(20)
+    with pytest.raises(lbm.LbmError) as err:
+        s.observables()
+    assert err.value.status == lbm.LBM_ENAN
+    obs = s.observables(allow_nan=True)
+    assert obs[0]["nonfinite"] == 0 and obs[1]["nonfinite"] == 1
+    np.testing.assert_array_equal(s.populations(0), alone.populations())
+    s.close()
+    alone.close()
