@@ -10,8 +10,6 @@ from __future__ import annotations
 import json
 import time
 
-import numpy as np
-
 from . import inputs as I
 from . import lbm
 

@@ -2,10 +2,7 @@
 the CUDA library (via its C ABI) and through the FP64 oracle, and compare."""
 import numpy as np
 
-from oracle import analysis as A
 from oracle.lattice import Lattice, Params
-from paper_1309_6726_gb300 import inputs as I
-from paper_1309_6726_gb300 import lbm
 
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 W22 = np.concatenate([W9, W9, [0.25] * 4])
@@ -29,13 +26,3 @@ def pop_error(f_gpu, f_ora, scale_rho=1.0):
     d = np.abs(f_gpu.astype(np.float64) - f_ora) / (W22[:, None, None] *
                                                    scale_rho)
     return float(d.max())
-
-
-def elementwise_rel(f_gpu, f_ora, floor):
-    """max |d| / max(|f_oracle|, floor * w_i)."""
-    den = np.maximum(np.abs(f_ora), floor * W22[:, None, None])
-    return float((np.abs(f_gpu.astype(np.float64) - f_ora) / den).max())
-
-
-def gpu_observables_vs_oracle(obs_gpu, lat):
-    return obs_gpu, A.lattice_observables(lat)

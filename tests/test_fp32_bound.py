@@ -13,7 +13,6 @@ import ctypes as C
 import subprocess
 
 import numpy as np
-import pytest
 
 from oracle import build as B
 from paper_1309_6726_gb300 import inputs as I

@@ -13,7 +13,6 @@ stated with its test.  Integer and index results -- the solid mask, the
 step a node turns solid, the pore-closure step -- must match exactly; the
 front position within 0.5 lattice units.
 """
-import os
 
 import numpy as np
 import pytest
@@ -21,8 +20,7 @@ import pytest
 from oracle import analysis as A
 from paper_1309_6726_gb300 import inputs as I
 from paper_1309_6726_gb300 import lbm
-from tests.gpu_helpers import (elementwise_rel, oracle_for, oracle_pops,
-                               pop_error)
+from tests.gpu_helpers import oracle_for, oracle_pops, pop_error
 
 pytestmark = pytest.mark.gpu
 
