@@ -38,9 +38,9 @@ METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated err
 #: algorithmic bytes per fluid-node update of the step kernel: each stored
 #: element read once and written once, the mask byte read once.
 #: FP32: 22 populations x 4 B x 2 = 176, + 1 mask byte.
-#: FP16: 20 deviations x 2 B x 2 = 80, 3 references x 2 B x 2 = 12,
+#: FP16: 20 deviations x 2 B x 2 = 80, 5 references x 2 B x 2 = 20,
 #: 2 FP32 rest populations x 4 B x 2 = 16, + 1.
-BYTES_PER_NODE = {"fp32": 177.0, "fp16": 109.0}
+BYTES_PER_NODE = {"fp32": 177.0, "fp16": 117.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel
@@ -49,7 +49,7 @@ DEPOSIT_BYTES = 16.0
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 117.15}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 126.79}
 
 
 def load_peaks():

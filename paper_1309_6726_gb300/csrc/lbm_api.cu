@@ -299,7 +299,7 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                           std::to_string((int)r);
                     return false;
                 }
-                // FP32 rest planes after the 3 reference planes of the block
+                // FP32 rest planes after the 5 reference planes of the block
                 const int64_t g0 = (int64_t)GHOST * d.pitch + XGHOST;
                 char *rbase = (char *)h->d_mom[b] +
                               (size_t)((d.mom_off - g0) + NMOM * d.plane) * 2;
@@ -939,7 +939,7 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
 
 // ---- checkpoints -----------------------------------------------------------
 
-static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '2'};
+static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '3'};
 
 struct CkptHeader {
     char magic[8];

@@ -21,8 +21,9 @@ __device__ __forceinline__ float load_pop(const void *base, const __half *mom,
     const float dv =
         __half2float(static_cast<const __half *>(base)[d.pop_off + sp16(q) * d.plane + e]);
     const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
-    const float rt = __half2float(mom[d.mom_off + comp * d.plane + e]);
-    return comp < 2 ? dec_pop(q - comp * Q, dv, rt) : dec_sol(dv, rt);
+    if (comp == 2) return dec_sol(dv, __half2float(mom[d.mom_off + kSolRef * d.plane + e]));
+    const int i = q - comp * Q;
+    return dec_pop(i, dv, __half2float(mom[d.mom_off + refp(comp, i) * d.plane + e]));
 }
 
 // Post-streaming populations of node (x, y) at the current step: 22 values

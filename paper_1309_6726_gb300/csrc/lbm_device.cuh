@@ -8,9 +8,9 @@
 //     starts on a 128-byte boundary in FP32 storage);
 //   FP16 storage keeps 20 FP16 planes per lattice (the 8 moving A and 8
 //     moving B populations, then the 4 solute ones, see sp16) and, per
-//     lattice and buffer, a moment block of 3 FP16 reference planes
-//     (rho~_A, rho~_B, C~) followed by 2 FP32 planes holding the rest
-//     populations of A and B (rest_planes);
+//     lattice and buffer, a moment block of 5 FP16 reference planes
+//     (w_1 rho~ and w_5 rho~ of A and of B, C~ / 4, see refp) followed by
+//     2 FP32 planes holding the rest populations of A and B (rest_planes);
 //   every plane (populations, moments, mask) has a two-node ghost band
 //     around the lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx,
 //     nx + 1 -- holding the periodic images of the nodes next to the
@@ -35,16 +35,21 @@ namespace lbmk {
 constexpr int Q = 9;      // D2Q9 per fluid component
 constexpr int QS = 4;     // D2Q4 solute
 constexpr int NPOP = 22;  // 9 + 9 + 4 planes per lattice
-constexpr int NMOM = 3;   // FP16 storage: rho~_A, rho~_B, C~ planes
+constexpr int NMOM = 5;   // FP16 storage: reference planes (see refp)
 constexpr int NP16 = 20;  // FP16 storage: population planes (no rest ones)
 constexpr int NREST = 2;  // FP16 storage: FP32 rest planes of A and B
-// FP16 storage: the moment block of a lattice spans 7 half-planes, the 3
+// FP16 storage: the moment block of a lattice spans 9 half-planes, the 5
 // FP16 references then the 2 FP32 rest planes
 constexpr int MOM_BLOCK = NMOM + 2 * NREST;
 
 // FP16 storage plane of population q (A: 1..8, B: 10..17, solute 18..21;
 // the rest populations 0 and 9 are FP32, in the moment block)
 __host__ __device__ constexpr int sp16(int q) { return q < Q ? q - 1 : q - 2; }
+// FP16 storage reference plane of moving population i (1..8) of component
+// comp: w_1 rho~ and w_5 rho~ of A (planes 0, 1) and of B (2, 3); the
+// solute's C~ / 4 is plane kSolRef
+__host__ __device__ constexpr int refp(int comp, int i) { return 2 * comp + (i >= 5 ? 1 : 0); }
+constexpr int kSolRef = 4;
 
 // D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
 __host__ __device__ __forceinline__ constexpr int cx(int i) {
@@ -150,62 +155,69 @@ constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
 // ---- FP16 storage codec ------------------------------------------------------
-// A component's moving populations are kept as FP16 deviations from a
-// per-node reference rho~ (FP16, stored once per node and component), the
+// A component's moving populations are kept as FP16 deviations from per-node
+// references (FP16, stored once per node, component and weight class), the
 // solute likewise; the rest population is kept in FP32:
-//   moving i = 1..8:  d = 2^10 (f_i / w_i - rho~),  f_i = w_i (rho~ + 2^-10 d)
-//   solute k = 0..3:  d = 2^10 (4 g_k - C~),        g_k = (C~ + 2^-10 d) / 4
-//   rest:             f_0 in FP32, the density minus the moving read-backs
-// The power-of-two scale is exact; it lifts the minority component's small
-// deviations out of FP16's subnormal range (|d| stays far below 65504).
-// Every read rounds exactly as written here (no contraction into later
-// sums), so all code paths rebuild the same FP32 value from the same bits.
+//   moving i = 1..8:  r_c = FP16(w_c rho~) for the class c of i (w_1 or w_5),
+//                     d = 2^10 (f_i - r_c) / w_i,  f_i = r_c + (w_i 2^-10) d
+//   solute k = 0..3:  r = FP16(C / 4),  d = 2^12 (g_k - r),  g_k = r + 2^-12 d
+//   rest:             f_0 in FP32, taking up the moving values' rounding
+// The power-of-two scales are exact; they lift the minority component's
+// small deviations out of FP16's subnormal range (|d| stays far below
+// 65504).  Reading is one fused multiply-add per value, rounded exactly as
+// written here (no contraction into later sums), so all code paths rebuild
+// the same FP32 value from the same bits.
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
+constexpr float kSolScale = 4096.0f;
+constexpr float kInvSolScale = 1.0f / 4096.0f;
 
-// Moving population i (1..8) of a D2Q9 component from its deviation and
-// reference.
-__device__ __forceinline__ float dec_pop(int i, float d, float rt) {
-    return __fmul_rn(wq(i), __fmaf_rn(d, kInvDevScale, rt));
+// Moving population i (1..8) of a D2Q9 component from its deviation and the
+// reference of its weight class.
+__device__ __forceinline__ float dec_pop(int i, float d, float ref) {
+    return __fmaf_rn(d, wq(i) * kInvDevScale, ref);
 }
 // A solute population from its deviation and reference.
-__device__ __forceinline__ float dec_sol(float d, float ct) {
-    return __fmul_rn(0.25f, __fmaf_rn(d, kInvDevScale, ct));
+__device__ __forceinline__ float dec_sol(float d, float ref) {
+    return __fmaf_rn(d, kInvSolScale, ref);
 }
 
 // Encodes the 9 post-collision populations of one component: the moving
-// deviations into dq[1..8], the rest population into `rest`; returns the
-// reference.  rho~ = f_0 / w_0 rounded to FP16 (the density times
-// 1 - 3/2 u.u at equilibrium), so every deviation is small.  The rest
-// population takes up the quantisation error of the eight moving ones --
-// each error f_i - read-back(f_i) is exact in FP32 and tiny, and readers
-// round the read-back exactly as here -- so the stored mass is the FP32
-// mass up to one rounding at f_0's magnitude.  (Solving the rest
-// population from an FP32 sum of all nine values instead biased the mass
-// of long runs by about 1e-8 per step: populations near w_i rho share
-// their low-order bits, so the roundings of such sums are not unbiased.)
-__device__ __forceinline__ __half enc9(const float f[Q], __half dq[Q],
-                                       float &rest) {
-    const __half rh = __float2half_rn(f[0] * (1.0f / wq(0)));
-    const float rt = __half2float(rh);
-    const float nrt = -kDevScale * rt;
+// deviations into dq[1..8], the references of the two weight classes into
+// h1 (w_1 rho~) and h5 (w_5 rho~), the rest population into `rest`.
+// rho~ = f_0 / w_0 (the density times 1 - 3/2 u.u at equilibrium), so every
+// deviation is small.  The rest population takes up the quantisation error
+// of the eight moving ones -- each error f_i - read-back(f_i) is exact in
+// FP32 and tiny, and readers round the read-back exactly as here -- so the
+// stored mass is the FP32 mass up to one rounding at f_0's magnitude.
+// (Solving the rest population from an FP32 sum of all nine values instead
+// biased the mass of long runs by about 1e-8 per step: populations near
+// w_i rho share their low-order bits, so the roundings of such sums are not
+// unbiased.)
+__device__ __forceinline__ void enc9(const float f[Q], __half dq[Q],
+                                     __half &h1, __half &h5, float &rest) {
+    const float rt = f[0] * (1.0f / wq(0));
+    h1 = __float2half_rn(wq(1) * rt);
+    h5 = __float2half_rn(wq(5) * rt);
+    const float ref1 = __half2float(h1), ref5 = __half2float(h5);
+    const float n1 = -ref1 * (kDevScale / wq(1)), n5 = -ref5 * (kDevScale / wq(5));
     float err = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        dq[i] = __float2half_rn(__fmaf_rn(f[i], kDevScale / wq(i), nrt));
-        err += f[i] - dec_pop(i, __half2float(dq[i]), rt);
+        const float ref = i < 5 ? ref1 : ref5;
+        dq[i] = __float2half_rn(__fmaf_rn(f[i], kDevScale / wq(i), i < 5 ? n1 : n5));
+        err += f[i] - dec_pop(i, __half2float(dq[i]), ref);
     }
     rest = f[0] + err;
-    return rh;
 }
 
-// Encodes the 4 solute populations; returns the reference C~.
+// Encodes the 4 solute populations; returns the reference C~ / 4.
 __device__ __forceinline__ __half enc4(const float g[QS], __half dq[QS]) {
     const float c = (g[0] + g[2]) + (g[1] + g[3]);
-    const __half ch = __float2half_rn(c);
+    const __half ch = __float2half_rn(0.25f * c);
     const float ct = __half2float(ch);
 #pragma unroll
-    for (int k = 0; k < QS; ++k) dq[k] = __float2half_rn((4.0f * g[k] - ct) * kDevScale);
+    for (int k = 0; k < QS; ++k) dq[k] = __float2half_rn((g[k] - ct) * kSolScale);
     return ch;
 }
 
@@ -226,8 +238,8 @@ constexpr int XGHOST = 16;  // physical columns before logical column 0
 
 // FP16 storage: the FP32 rest planes of lattice d (A, then B, `plane`
 // apart), at its logical node (0, 0), inside the moment block that starts
-// 3 planes before them.  Both the block start (a multiple of 7 planes of
-// halves) and the 3 reference planes keep them 16-byte aligned.
+// 5 planes before them.  Both the block start (a multiple of 9 planes of
+// halves) and the 5 reference planes keep them 16-byte aligned.
 __device__ __forceinline__ float *rest_planes(__half *mom, const LatDesc &d) {
     const int64_t g = (int64_t)GHOST * d.pitch + XGHOST;
     return reinterpret_cast<float *>(mom + (d.mom_off - g) + NMOM * d.plane) + g;

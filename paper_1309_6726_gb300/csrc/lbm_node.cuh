@@ -97,8 +97,8 @@ __device__ __forceinline__ void store22_f32(float *__restrict__ p, int plane,
 }
 
 // FP16 storage: the 20 FP16 deviations of a node at p[sp16(q) * plane],
-// its 3 references at mp[c * plane] and its 2 FP32 rest populations at
-// rp[c * rplane].
+// its 5 references at mp[refp(c, i) * plane] and mp[kSolRef * plane] and
+// its 2 FP32 rest populations at rp[c * rplane].
 __device__ __forceinline__ void store22_f16(__half *__restrict__ p,
                                             __half *__restrict__ mp,
                                             float *__restrict__ rp, int plane,
@@ -107,15 +107,20 @@ __device__ __forceinline__ void store22_f16(__half *__restrict__ p,
                                             const float g[QS]) {
     __half dq[Q];
     float rest;
-    mp[0] = enc9(fA, dq, rest);
+    __half h1, h5;
+    enc9(fA, dq, h1, h5, rest);
+    mp[refp(0, 1) * plane] = h1;
+    mp[refp(0, 5) * plane] = h5;
     rp[0] = rest;
 #pragma unroll
     for (int i = 1; i < Q; ++i) p[sp16(i) * plane] = dq[i];
-    mp[plane] = enc9(fB, dq, rest);
+    enc9(fB, dq, h1, h5, rest);
+    mp[refp(1, 1) * plane] = h1;
+    mp[refp(1, 5) * plane] = h5;
     rp[rplane] = rest;
 #pragma unroll
     for (int i = 1; i < Q; ++i) p[sp16(Q + i) * plane] = dq[i];
-    mp[2 * plane] = enc4(g, dq);
+    mp[kSolRef * plane] = enc4(g, dq);
 #pragma unroll
     for (int k = 0; k < QS; ++k) p[sp16(2 * Q + k) * plane] = dq[k];
 }
@@ -139,7 +144,7 @@ __device__ __forceinline__ void store_node22(const StepArgs &a,
 
 // Writes the 22 post-collision values of the tile node at `o` (planes NT
 // apart) -- a shared-memory tile that bulk tensor stores then copy out:
-// FP32 [22][NT]; FP16 [20][NT] deviations, om [3][NT] references, orest
+// FP32 [22][NT]; FP16 [20][NT] deviations, om [5][NT] references, orest
 // [2][NT] rest populations.
 template <class S, int NT>
 __device__ __forceinline__ void store_tile22(typename S::T *o, __half *om,

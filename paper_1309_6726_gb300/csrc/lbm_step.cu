@@ -69,8 +69,9 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
             f[0] = rest_planes(mom, d)[comp * d.plane + own];
         } else {
             const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
-            const float rt = __half2float(mom[d.mom_off + comp * d.plane + src]);
-            f[i] = dec_pop(qi, dv, rt);
+            // opposite directions share a weight class: i's reference
+            const float rt = __half2float(mom[d.mom_off + refp(comp, i) * d.plane + src]);
+            f[i] = dec_pop(i, dv, rt);
         }
     }
 }
@@ -95,7 +96,7 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
             g[k] = __ldg(fin + d.pop_off + q * d.plane + src);
         } else {
             const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
-            const float ct = __half2float(mom[d.mom_off + 2 * d.plane + src]);
+            const float ct = __half2float(mom[d.mom_off + kSolRef * d.plane + src]);
             g[k] = dec_sol(dv, ct);
         }
     }

@@ -8,7 +8,7 @@
 //     copy (cp.async.bulk.tensor) of the population planes over the tile
 //     plus a halo of 2 rows and 4 (FP32) or 8 (FP16) columns -- the x start
 //     stays 16-byte aligned -- into shared memory, completing on an
-//     mbarrier; FP16 storage adds copies of the 3 reference planes and the
+//     mbarrier; FP16 storage adds copies of the 5 reference planes and the
 //     2 FP32 rest planes; the mask box and the lattice descriptor come
 //     with them;
 //   * two stages: the copy of the next tile is in flight while the current
@@ -147,7 +147,7 @@ struct TmaTile {
     static constexpr int MXO = 16;                // mask box: 16-byte aligned
     static constexpr int MBX = TX + 2 * MXO;
     // population planes in a stage: 22 FP32, or 20 FP16 deviations plus
-    // 3 FP16 references and 2 FP32 rest planes
+    // 5 FP16 references and 2 FP32 rest planes
     static constexpr int NPL = S::kHalf ? NP16 : NPOP;
     static constexpr int POP_BYTES = NPL * PL * (int)sizeof(T);
     static constexpr int MOM_BYTES = S::kHalf ? NMOM * PL * 2 : 0;
@@ -172,7 +172,7 @@ struct TmaTile {
     static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
     static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
     // The tile's post-collision output, [22][TY][TX] FP32 or [20][TY][TX]
-    // FP16 + [3][TY][TX] FP16 references + [2][TY][TX] FP32 rest planes,
+    // FP16 + [5][TY][TX] FP16 references + [2][TY][TX] FP32 rest planes,
     // written by bulk tensor stores -- where it fits.
     static constexpr int OUT_POP = NPL * NT * (int)sizeof(T);
     static constexpr int OUT_REST = OUT_POP + (S::kHalf ? NMOM * NT * 2 : 0);
@@ -213,8 +213,9 @@ __device__ __forceinline__ void spull9(const typename S::T *tile,
         } else if (i == 0) {
             f[0] = rest[comp * TT::PL + c];
         } else {
-            f[i] = dec_pop(qi, __half2float(tile[sp16(comp * Q + qi) * TT::PL + cell]),
-                           __half2float(mom[comp * TT::PL + cell]));
+            // opposite directions share a weight class: i's reference
+            f[i] = dec_pop(i, __half2float(tile[sp16(comp * Q + qi) * TT::PL + cell]),
+                           __half2float(mom[refp(comp, i) * TT::PL + cell]));
         }
     }
 }
@@ -232,7 +233,7 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
             g[k] = tile[q * TT::PL + cell];
         } else {
             g[k] = dec_sol(__half2float(tile[sp16(q) * TT::PL + cell]),
-                           __half2float(mom[2 * TT::PL + cell]));
+                           __half2float(mom[kSolRef * TT::PL + cell]));
         }
     }
 }
