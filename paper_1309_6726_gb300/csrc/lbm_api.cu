@@ -379,12 +379,24 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
         why = std::string("TMA kernel setup: ") + cudaGetErrorString(e);
         return false;
     }
-    struct Strip { int lat, col, rows; };
+    // A strip is a run of tiles down one tile column of a lattice (the
+    // halo rows each tile copies were just copied by the tile above it).
+    // Columns taller than a quarter of a block's share are cut into
+    // segments, so that a few tall lattices (a 2048-row preform: 32
+    // columns of 256 tiles) still spread over every block.
+    struct Strip { int lat, col, row0, rows; };
+    long long total = 0;
+    for (int l = 0; l < h->count; ++l)
+        total += (long long)h->desc[l].tiles_x * ((h->desc[l].ny + h->ty - 1) / h->ty);
+    const long long seg =
+        std::max(4LL, (total + 4LL * grid - 1) / (4LL * grid));
     std::vector<Strip> strips;
     for (int l = 0; l < h->count; ++l) {
         const LatDesc &d = h->desc[l];
         const int rows = (d.ny + h->ty - 1) / h->ty;
-        for (int c = 0; c < d.tiles_x; ++c) strips.push_back({l, c, rows});
+        for (int c = 0; c < d.tiles_x; ++c)
+            for (int r0 = 0; r0 < rows; r0 += (int)seg)
+                strips.push_back({l, c, r0, (int)std::min<long long>(seg, rows - r0)});
     }
     std::stable_sort(strips.begin(), strips.end(),
                      [](const Strip &a, const Strip &b) { return a.rows > b.rows; });
@@ -398,7 +410,7 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
     for (const Strip &st : strips) {
         std::pop_heap(heap.begin(), heap.end(), less);
         const int b = heap.back();
-        for (int r = 0; r < st.rows; ++r)
+        for (int r = st.row0; r < st.row0 + st.rows; ++r)
             lists[b].push_back(TileRec{st.lat, st.col * h->tx, r * h->ty, 0});
         load[b] += st.rows;
         std::push_heap(heap.begin(), heap.end(), less);

@@ -347,9 +347,9 @@ __global__ void __launch_bounds__(TX *TY)
     TileRec *s_rec = reinterpret_cast<TileRec *>(bar + 4);  // tile of each desc slot
 
     // This block's tiles: sched[blockIdx.x + k * gridDim.x], k = 0, 1, ...,
-    // until the first -1; consecutive entries walk down one tile column of a
-    // lattice, so the halo rows a tile copies were copied by the previous
-    // tile of the same block and come from L2.
+    // until the first -1; consecutive entries mostly walk down one tile
+    // column of a lattice, so the halo rows a tile copies were copied by the
+    // previous tile of the same block and come from L2.
     auto sched_at = [&](int k) {
         return k < nslots ? sched[blockIdx.x + (size_t)k * gridDim.x]
                           : TileRec{-1, 0, 0, 0};
