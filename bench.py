@@ -49,7 +49,7 @@ DEPOSIT_BYTES = 16.0
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.69, "fp16": 126.79}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.52, "fp16": 126.90}
 
 
 def load_peaks():

@@ -188,7 +188,10 @@ struct TmaTile {
                       REST_OFF % 16 == 0 && OUT_REST % 16 == 0,
                   "stage alignment");
     static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
-    static constexpr int RW = (NRING + NW - 1) / NW;  // ring cells per warp
+    // ring cells per warp: whole warps take the ring (5 of 8 at 64 x 4),
+    // since a warp costs the same issue slots with 10 lanes active as with
+    // 32 (spreading it thinly over every warp measured 4 % slower for FP16)
+    static constexpr int RW = 32;
     static_assert(NRING <= NT && RW <= 32, "ring spread");
     static_assert(TX % 32 == 0, "a warp covers 32 columns of one row");
 };
@@ -238,13 +241,16 @@ __device__ __forceinline__ void spull4(const typename S::T *tile,
     }
 }
 
-// The 22 populations of the node at stage cell c.
+// The 22 populations of the node at stage cell c.  `fast` (bb == 0 on
+// every lane that calls) takes the path without bounce-back selects; the
+// other path gives the same values for bb == 0, so a warp with any
+// bounce-back lane runs that one alone.
 template <class S, class TT>
 __device__ __forceinline__ void spull22(const typename S::T *tile,
                                         const __half *mom, const float *rest,
-                                        int c, unsigned bb, float fA[Q],
-                                        float fB[Q], float g[QS]) {
-    if (bb == 0u) {
+                                        int c, unsigned bb, bool fast,
+                                        float fA[Q], float fB[Q], float g[QS]) {
+    if (fast) {
         spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, fA);
         spull9<S, TT, false>(tile, mom, rest, 1, c, 0u, fB);
         spull4<S, TT, false>(tile, mom, c, 0u, g);
@@ -255,16 +261,16 @@ __device__ __forceinline__ void spull22(const typename S::T *tile,
     }
 }
 
-// Densities of both components at stage cell c.
+// Densities of both components at stage cell c (`fast` as for spull22).
 template <class S, class TT>
 __device__ __forceinline__ void sdens(const typename S::T *tile,
                                       const __half *mom, const float *rest,
-                                      int c, unsigned bb, float &ra,
-                                      float &rb) {
+                                      int c, unsigned bb, bool fast,
+                                      float &ra, float &rb) {
     float f[Q];
     ra = 0.f;
     rb = 0.f;
-    if (bb == 0u) {
+    if (fast) {
         spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) ra += f[i];
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(TX *TY)
         {
             float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
-                spull22<S, TT>(tp, tm, tr, pc, bb, fA, fB, g);
+                spull22<S, TT>(tp, tm, tr, pc, bb, clean, fA, fB, g);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
             }
@@ -480,9 +486,9 @@ __global__ void __launch_bounds__(TX *TY)
             fr[(ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : ra;
             fr[TT::RX * TT::RY + (ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : rb;
         }
-        // ring of the density frame, spread over the warps: the first RW
-        // lanes of each warp take RW consecutive ring cells (consecutive
-        // addresses, no shared-memory bank conflicts)
+        // ring of the density frame: the lanes of the first warps take
+        // RW consecutive ring cells each (consecutive addresses, no
+        // shared-memory bank conflicts)
         {
             const int r = warp * TT::RW + lane;
             if (lane < TT::RW && r < TT::NRING) {
@@ -495,8 +501,9 @@ __global__ void __launch_bounds__(TX *TY)
                 const int rpc = (ry + 1) * TT::BX + rx - 1 + TT::XO;
                 float ra = 0.f, rb = 0.f;
                 if (!(sm[rmc] & mb.force)) {
+                    // per lane: a warp-uniform choice here measured slower
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
-                    sdens<S, TT>(tp, tm, tr, rpc, rbb, ra, rb);
+                    sdens<S, TT>(tp, tm, tr, rpc, rbb, rbb == 0u, ra, rb);
                 }
                 fr[ry * TT::RX + rx] = ra;
                 fr[TT::RX * TT::RY + ry * TT::RX + rx] = rb;
