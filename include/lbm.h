@@ -231,6 +231,25 @@ lbm_status lbm_fit_reff(const double *t, const double *z, int32_t n,
                         double gamma, double mu, double length,
                         double cos_theta0, double *r_eff);
 
+/* Tile schedule of the TMA-staged step kernel (project addition; the paper
+ * describes no implementation), computed on the host as lbm_create computes
+ * it: the tiles of tx by ty nodes of `count` lattices of nx[l] by ny[l]
+ * nodes, dealt to `grid` persistent blocks.  A strip is a run of tiles down
+ * one tile column of a lattice; columns longer than
+ * max(4, ceil(tiles / (4 grid))) tiles are cut into strips of that length,
+ * and strips go, longest first, to the block with the fewest tiles so far
+ * (ties to the lower index).  Block b's k-th tile is written to
+ * out[3 * (k * grid + b) + 0, 1, 2] = lattice, first column, first row;
+ * lattice -1 (columns and rows 0) follows a block's last tile.  *slots
+ * receives the longest list, so out holds 3 * grid * *slots values; out may
+ * be NULL to query *slots alone, else it holds cap int32 values
+ * (LBM_EINVAL when fewer than needed).  LBM_EINVAL for NULL nx, ny or
+ * slots, count, tx, ty or grid < 1, or a lattice size < 1.  Host-only
+ * arithmetic: needs no GPU. */
+lbm_status lbm_plan_tiles(const int32_t *nx, const int32_t *ny, int32_t count,
+                          int32_t tx, int32_t ty, int32_t grid, int32_t *out,
+                          int64_t cap, int32_t *slots);
+
 /* ---- observables without allocation ----------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

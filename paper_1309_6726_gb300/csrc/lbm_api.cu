@@ -367,34 +367,27 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     return true;
 }
 
-// Tile schedule of the persistent TMA kernel: the tile columns ("strips")
-// of every lattice are dealt to the `grid` blocks, each to the block with
-// the least work so far (longest strips first); block b then walks its
+// Tile schedule of the persistent TMA kernel, host arithmetic only.  A
+// strip is a run of tiles down one tile column of a lattice (the halo rows
+// each tile copies were just copied by the tile above it).  Columns taller
+// than a quarter of a block's share (at least 4 tiles) are cut into strips
+// of that length, so that a few tall lattices (a 2048-row preform: 32
+// columns of 256 tiles) still spread over every block.  Strips go, longest
+// first, to the block with the least work so far; block b then walks its
 // strips top to bottom, its k-th tile at sched[b + k * grid] (lattice -1 =
-// done).
-static bool make_schedule(lbm_handle *h, std::string &why) {
-    int grid = 0;
-    cudaError_t e = grid_step_tma(h->tx, h->ty, h->half, &grid);
-    if (e != cudaSuccess || grid <= 0) {
-        why = std::string("TMA kernel setup: ") + cudaGetErrorString(e);
-        return false;
-    }
-    // A strip is a run of tiles down one tile column of a lattice (the
-    // halo rows each tile copies were just copied by the tile above it).
-    // Columns taller than a quarter of a block's share are cut into
-    // segments, so that a few tall lattices (a 2048-row preform: 32
-    // columns of 256 tiles) still spread over every block.
+// done).  Returns the slots per block.
+static size_t plan_tiles(const int32_t *nx, const int32_t *ny, int count,
+                         int tx, int ty, int grid, std::vector<TileRec> &sched) {
     struct Strip { int lat, col, row0, rows; };
     long long total = 0;
-    for (int l = 0; l < h->count; ++l)
-        total += (long long)h->desc[l].tiles_x * ((h->desc[l].ny + h->ty - 1) / h->ty);
+    for (int l = 0; l < count; ++l)
+        total += (long long)((nx[l] + tx - 1) / tx) * ((ny[l] + ty - 1) / ty);
     const long long seg =
         std::max(4LL, (total + 4LL * grid - 1) / (4LL * grid));
     std::vector<Strip> strips;
-    for (int l = 0; l < h->count; ++l) {
-        const LatDesc &d = h->desc[l];
-        const int rows = (d.ny + h->ty - 1) / h->ty;
-        for (int c = 0; c < d.tiles_x; ++c)
+    for (int l = 0; l < count; ++l) {
+        const int cols = (nx[l] + tx - 1) / tx, rows = (ny[l] + ty - 1) / ty;
+        for (int c = 0; c < cols; ++c)
             for (int r0 = 0; r0 < rows; r0 += (int)seg)
                 strips.push_back({l, c, r0, (int)std::min<long long>(seg, rows - r0)});
     }
@@ -411,15 +404,32 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
         std::pop_heap(heap.begin(), heap.end(), less);
         const int b = heap.back();
         for (int r = st.row0; r < st.row0 + st.rows; ++r)
-            lists[b].push_back(TileRec{st.lat, st.col * h->tx, r * h->ty, 0});
+            lists[b].push_back(TileRec{st.lat, st.col * tx, r * ty, 0});
         load[b] += st.rows;
         std::push_heap(heap.begin(), heap.end(), less);
     }
     size_t slots = 0;
     for (auto &v : lists) slots = std::max(slots, v.size());
-    std::vector<TileRec> sched((size_t)grid * slots, TileRec{-1, 0, 0, 0});
+    sched.assign((size_t)grid * slots, TileRec{-1, 0, 0, 0});
     for (int b = 0; b < grid; ++b)
         for (size_t k = 0; k < lists[b].size(); ++k) sched[b + k * grid] = lists[b][k];
+    return slots;
+}
+
+static bool make_schedule(lbm_handle *h, std::string &why) {
+    int grid = 0;
+    cudaError_t e = grid_step_tma(h->tx, h->ty, h->half, &grid);
+    if (e != cudaSuccess || grid <= 0) {
+        why = std::string("TMA kernel setup: ") + cudaGetErrorString(e);
+        return false;
+    }
+    std::vector<int32_t> nx(h->count), ny(h->count);
+    for (int l = 0; l < h->count; ++l) {
+        nx[l] = h->desc[l].nx;
+        ny[l] = h->desc[l].ny;
+    }
+    std::vector<TileRec> sched;
+    const size_t slots = plan_tiles(nx.data(), ny.data(), h->count, h->tx, h->ty, grid, sched);
     if (cudaMalloc(&h->d_sched, std::max<size_t>(sched.size(), 1) * sizeof(TileRec)) != cudaSuccess ||
         cudaMemcpy(h->d_sched, sched.data(), sched.size() * sizeof(TileRec),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1051,6 +1061,29 @@ extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
     fclose(f);
     if (!ok) return fail(h, LBM_EIO, std::string("read failed: ") + path);
     h->steps = hd.steps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_plan_tiles(const int32_t *nx, const int32_t *ny,
+                                     int32_t count, int32_t tx, int32_t ty,
+                                     int32_t grid, int32_t *out, int64_t cap,
+                                     int32_t *slots) {
+    if (!nx || !ny || !slots || count < 1 || tx < 1 || ty < 1 || grid < 1)
+        return fail(nullptr, LBM_EINVAL, "plan_tiles: NULL array, count, tile or grid < 1");
+    for (int l = 0; l < count; ++l)
+        if (nx[l] < 1 || ny[l] < 1)
+            return fail(nullptr, LBM_EINVAL, "plan_tiles: lattice size < 1");
+    std::vector<TileRec> sched;
+    const size_t n = plan_tiles(nx, ny, count, tx, ty, grid, sched);
+    *slots = (int32_t)n;
+    if (!out) return LBM_OK;
+    if ((int64_t)sched.size() * 3 > cap)
+        return fail(nullptr, LBM_EINVAL, "plan_tiles: output holds fewer than 3 * grid * slots values");
+    for (size_t k = 0; k < sched.size(); ++k) {
+        out[3 * k] = sched[k].lat;
+        out[3 * k + 1] = sched[k].lat >= 0 ? sched[k].x0 : 0;
+        out[3 * k + 2] = sched[k].lat >= 0 ? sched[k].y0 : 0;
+    }
     return LBM_OK;
 }
 

@@ -25,7 +25,7 @@ SYMBOLS = ("lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_step",
            "lbm_get_solid_mask", "lbm_get_fields", "lbm_set_fields",
            "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
            "lbm_fit_reff", "lbm_observables_static", "lbm_autotune",
-           "lbm_get_tuning")
+           "lbm_get_tuning", "lbm_plan_tiles")
 
 
 class LbmError(RuntimeError):
@@ -115,6 +115,9 @@ def load_library(path: str = LIB_PATH):
     dp = C.POINTER(C.c_double)
     lib.lbm_fit_reff.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double,
                                  C.c_double, C.c_double, dp]
+    ip = C.POINTER(C.c_int32)
+    lib.lbm_plan_tiles.argtypes = [ip, ip, C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int32, ip, C.c_int64, ip]
     lib.lbm_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
     lib.lbm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     lib.lbm_observables_static.argtypes = [vp, vp, vp, vp, C.c_int32,
@@ -294,6 +297,28 @@ def fit_reff(t, z, gamma: float, mu: float, length: float,
     if st != LBM_OK:
         raise LbmError(st, "lbm_fit_reff: bad arguments")
     return out.value
+
+
+def plan_tiles(sizes, tx: int, ty: int, grid: int) -> np.ndarray:
+    """Tile schedule of the TMA step kernel (``lbm_plan_tiles``) for
+    lattices of (nx, ny) ``sizes``: int32 [slots, grid, 3] of (lattice,
+    first column, first row), lattice -1 after a block's last tile."""
+    lib = load_library()
+    nx = np.ascontiguousarray([s[0] for s in sizes], dtype=np.int32)
+    ny = np.ascontiguousarray([s[1] for s in sizes], dtype=np.int32)
+    ip = C.POINTER(C.c_int32)
+    slots = C.c_int32()
+    args = (nx.ctypes.data_as(ip), ny.ctypes.data_as(ip), len(nx), tx, ty,
+            grid)
+    st = lib.lbm_plan_tiles(*args, None, 0, C.byref(slots))
+    if st != LBM_OK:
+        raise LbmError(st, lib.lbm_last_error(None).decode())
+    out = np.empty((slots.value, grid, 3), dtype=np.int32)
+    st = lib.lbm_plan_tiles(*args, out.ctypes.data_as(ip), out.size,
+                            C.byref(slots))
+    if st != LBM_OK:
+        raise LbmError(st, lib.lbm_last_error(None).decode())
+    return out
 
 
 #: most columns lbm_observables_static accepts (its fixed scratch size)
