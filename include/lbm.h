@@ -63,10 +63,12 @@ typedef enum {
  * the deposit and the growth test are FP64 in both. */
 typedef enum {
     LBM_FP32 = 0, /* populations stored as FP32 */
-    LBM_FP16 = 1  /* populations stored as FP16 deviations from the lattice
-                     weight times a per-node FP16 reference (the node's own
-                     rest population per weight, kept in a moment plane);
-                     the rest deviation closes each node's mass */
+    LBM_FP16 = 1  /* moving populations and solute stored as FP16
+                     deviations from per-node FP16 references (w_1 rho~ and
+                     w_5 rho~ per component with rho~ = f_0 / w_0, C / 4 for
+                     the solute); the rest populations stay FP32 and take up
+                     the rounding of the moving ones, so each node keeps its
+                     mass to FP32 rounding */
 } lbm_precision;
 
 /* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,
@@ -206,7 +208,7 @@ typedef struct lbm_tuning {
 
 /* Autotuner for the step kernel (project addition; the paper describes no
  * implementation).  Times every supported variant (direct or TMA-staged,
- * tile shapes 32x4, 32x8, 32x16, 64x4, 64x8) for `steps` steps on this
+ * tile shapes 32x4, 32x8, 32x16, 64x4, 64x8, 128x4) for `steps` steps on this
  * handle's own state, restores the state after each trial, and keeps the
  * fastest; every variant computes bit-identical results, so only speed
  * differs.  Synchronizes; allocates a temporary copy of the state for the

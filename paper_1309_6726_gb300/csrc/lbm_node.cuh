@@ -15,14 +15,15 @@ namespace lbmk {
 //
 // Store32: plain FP32 planes.
 //
-// Store16: FP16 deviations from a per-node FP16 reference (enc9 / enc4 and
-// dec_pop / dec_sol in lbm_device.cuh).  The deviation is small next to rho
-// (it carries velocity and non-equilibrium parts only), so FP16's relative
-// precision applies to a quantity ~10-100x smaller than f_i itself; the
-// minority component (rho ~ 0.006) keeps the same relative accuracy as the
-// majority because the reference is local.  The rest deviation absorbs the
-// rounding of the eight others so that each node's stored mass equals its
-// FP32 mass.
+// Store16: FP16 deviations from per-node FP16 references, one per component
+// and weight class (enc9 / enc4 and dec_pop / dec_sol in lbm_device.cuh).
+// The deviation is small next to rho (it carries velocity and
+// non-equilibrium parts only), so FP16's relative precision applies to a
+// quantity ~10-100x smaller than f_i itself; the minority component
+// (rho ~ 0.006) keeps the same relative accuracy as the majority because the
+// references are local.  The FP32 rest population absorbs the rounding of
+// the eight moving ones so that each node's stored mass equals its FP32
+// mass up to one rounding.
 // ---------------------------------------------------------------------------
 
 struct Store32 {
