@@ -116,6 +116,46 @@ def pin_ledger(lib):
     return lat.ledger()[0] > 0 and np.allclose(tot(), t0, rtol=1e-12)
 
 
+def pin_threshold_inclusive(lib):
+    # reading c10: a node turns solid once its deposit reaches the threshold
+    # (m >= M_th).  At rest, k_r n_s C* = 0.25 * 1 * 0.5 = 0.125 exactly,
+    # landing the four D2Q4 neighbours of one solid node on m = 1.0.
+    n = 8
+    solid = np.zeros((n, n), np.uint8)
+    solid[4, 4] = 1
+    fl = solid == 0
+    ra = np.where(fl, 1.0, 0).astype(np.float32)
+    rb = np.where(fl, 0.006, 0).astype(np.float32)
+    cc = np.where(fl, 0.5, 0).astype(np.float32)
+    lat = Lattice(Params(g_coh=0.0, g_ads=0.0, k_r=0.25, m_threshold=1.0),
+                  solid, ra, rb, cc, lib=lib)
+    lat.set_deposit(np.where(fl, 0.875, 0.0))
+    lat.step(1)
+    s = lat.solid()
+    return (s.sum() == 5 and s[4, 3] == 1 and s[4, 5] == 1 and s[3, 4] == 1
+            and s[5, 4] == 1)
+
+
+def pin_solute_velocity(lib):
+    # readings c4 and c7: the solute is advected by u = (sum j + F/2) /
+    # sum rho.  From rest under a uniform acceleration gx, u = gx/2 in the
+    # first collision, and the solute's x-moment after one step is
+    # C u / tau_D.
+    n, gx, tau_d, c = 4, 1e-4, 0.8, 0.6
+    solid = np.zeros((n, n), np.uint8)
+    ra = np.full((n, n), 0.7, np.float32)
+    rb = np.full((n, n), 0.3, np.float32)
+    cc = np.full((n, n), c, np.float32)
+    lat = Lattice(Params(g_coh=0.0, g_ads=0.0, body_force_x=gx, tau_d=tau_d),
+                  solid, ra, rb, cc, lib=lib)
+    lat.step(1)
+    g = lat.solute()
+    mx = g[0] - g[2]
+    # C as the oracle holds it: the float32 input widened to FP64
+    return np.allclose(mx, float(np.float32(c)) * 0.5 * gx / tau_d,
+                       rtol=1e-9, atol=0)
+
+
 # (description, text in lbm_oracle.c, replacement, pin that must catch it)
 MUTANTS = [
     ("equilibrium: second-order coefficient 9/2 -> 3",
@@ -145,6 +185,12 @@ MUTANTS = [
      "static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, 1};", pin_mirror),
     ("growth forgets the deposit in the ledger",
      "L->ledger[3] += L->m[n];", "(void)0;", pin_ledger),
+    ("threshold test strict (m > M_th)",
+     "if (L->m[n] >= L->p.m_threshold) {", "if (L->m[n] > L->p.m_threshold) {",
+     pin_threshold_inclusive),
+    ("solute advected without the half-force term",
+     "L->u[0 * N + n] = rt > 0 ? (jx + 0.5 * Fx) / rt : 0.0;",
+     "L->u[0 * N + n] = rt > 0 ? jx / rt : 0.0;", pin_solute_velocity),
 ]
 
 
