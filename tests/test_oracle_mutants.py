@@ -156,6 +156,28 @@ def pin_solute_velocity(lib):
                        rtol=1e-9, atol=0)
 
 
+def pin_inlet(lib):
+    # reading c12: the inlet column x = 0 leaves each collision at the
+    # solute equilibrium of c_in (at rest: c_in / 4 per direction).  One
+    # step from C = 0 therefore puts c_in / 4 into the east-moving solute at
+    # x = 1, the west-moving one at x = nx - 1 (periodic), the two vertical
+    # ones at x = 0, and nothing anywhere else.
+    nx, ny, c_in = 8, 4, 0.8
+    solid = np.zeros((ny, nx), np.uint8)
+    ra = np.full((ny, nx), 1.0, np.float32)
+    rb = np.full((ny, nx), 0.006, np.float32)
+    lat = Lattice(Params(g_coh=0.0, g_ads=0.0, inlet=1, c_in=c_in), solid,
+                  ra, rb, ra * 0, lib=lib)
+    lat.step(1)
+    g = lat.solute()
+    expect = np.zeros((4, ny, nx))
+    expect[0, :, 1] = c_in / 4       # (1, 0)
+    expect[1, :, 0] = c_in / 4       # (0, 1)
+    expect[2, :, nx - 1] = c_in / 4  # (-1, 0)
+    expect[3, :, 0] = c_in / 4       # (0, -1)
+    return np.abs(g - expect).max() < 1e-15
+
+
 # (description, text in lbm_oracle.c, replacement, pin that must catch it)
 MUTANTS = [
     ("equilibrium: second-order coefficient 9/2 -> 3",
@@ -191,6 +213,12 @@ MUTANTS = [
     ("solute advected without the half-force term",
      "L->u[0 * N + n] = rt > 0 ? (jx + 0.5 * Fx) / rt : 0.0;",
      "L->u[0 * N + n] = rt > 0 ? jx / rt : 0.0;", pin_solute_velocity),
+    ("inlet on the second column",
+     "if (L->p.inlet && x == 0) {", "if (L->p.inlet && x == 1) {", pin_inlet),
+    ("inlet relaxes towards c_in instead of imposing it",
+     "for (int k = 0; k < QS; ++k) L->gc[k * N + n] = geq[k];",
+     "for (int k = 0; k < QS; ++k) L->gc[k * N + n] = L->g[k * N + n]"
+     " - (L->g[k * N + n] - geq[k]) / L->p.tau_d;", pin_inlet),
 ]
 
 
