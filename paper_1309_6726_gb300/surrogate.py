@@ -47,11 +47,20 @@ RATIO_RANGE = (0.6, 1.5)
 
 
 def time_grid(t_max: int, n: int = N_TIMES, t_first: int = T_FIRST) -> np.ndarray:
-    """n strictly increasing integer steps, log-spaced from t_first to t_max."""
-    t = np.unique(np.round(np.geomspace(t_first, t_max, n)).astype(np.int64))
-    while t.size < n:  # rounding merged neighbours: fill from the top
-        t = np.unique(np.concatenate([t, [t.max() + 1]]))
-    return t[:n]
+    """n strictly increasing integer steps, log-spaced from t_first to t_max
+    (both included).  Where rounding merges neighbours (a narrow range),
+    they are pushed apart within [t_first, t_max]; ValueError when fewer
+    than n integers lie in that range."""
+    if n < 2 or t_first < 1 or t_max - t_first + 1 < n:
+        raise ValueError("time_grid: need n >= 2 integers in [t_first, t_max]")
+    t = np.round(np.geomspace(t_first, t_max, n)).astype(np.int64)
+    t[0], t[-1] = t_first, t_max
+    for i in range(1, n):  # strictly increasing from the bottom ...
+        t[i] = max(t[i], t[i - 1] + 1)
+    t[-1] = t_max
+    for i in range(n - 2, -1, -1):  # ... and back under t_max from the top
+        t[i] = min(t[i], t[i + 1] - 1)
+    return t
 
 
 def draw_members(count: int, seed: int, length: int = 1024):

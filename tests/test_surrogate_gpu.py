@@ -63,16 +63,3 @@ def test_surrogate_learns_solver_trajectories_and_saves_time():
         tr["nonfinite"].sum(), len(train_m), te["nonfinite"].sum(),
         len(test_m), ref["nonfinite"].sum()))
     model.close()
-
-
-def test_time_grid_and_target_round_trip():
-    from paper_1309_6726_gb300 import surrogate as S
-    g = S.time_grid(20000)
-    assert g.size == 64 and g[0] == 100 and g[-1] == 20000
-    assert np.all(np.diff(g) > 0)
-    z = np.array([[1.0, 2.0], [3.0, np.nan]])
-    c = np.array([1234, -1])
-    y = S.targets(z, c, 20000)
-    zz, cc = S.decode(y, 20000)
-    np.testing.assert_allclose(zz[0], z[0], rtol=1e-6)
-    assert cc[0] == 1234 and cc[1] == -1
