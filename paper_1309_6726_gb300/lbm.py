@@ -157,10 +157,17 @@ class Solver:
         self.shapes = []
         for k, (g, p) in enumerate(zip(geoms, params)):
             solid = np.ascontiguousarray(g.solid, dtype=np.uint8)
+            if solid.ndim != 2:
+                raise ValueError("lattice %d: solid must be (ny, nx)" % k)
             ny, nx = solid.shape
             ra = np.ascontiguousarray(g.rho_a, dtype=np.float32)
             rb = np.ascontiguousarray(g.rho_b, dtype=np.float32)
             cc = np.ascontiguousarray(g.conc, dtype=np.float32)
+            # the library reads ny * nx values from each array
+            for name, a in (("rho_a", ra), ("rho_b", rb), ("conc", cc)):
+                if a.shape != solid.shape:
+                    raise ValueError("lattice %d: %s has shape %s, solid %s"
+                                     % (k, name, a.shape, solid.shape))
             self._keep += [solid, ra, rb, cc]
             G[k] = Geometry(nx, ny, solid.ctypes.data_as(C.POINTER(C.c_uint8)),
                             ra.ctypes.data_as(C.POINTER(C.c_float)),
@@ -256,7 +263,9 @@ class Solver:
     def set_populations(self, f, k: int = 0) -> None:
         a = np.ascontiguousarray(f, dtype=np.float32)
         ny, nx = self.shapes[k]
-        assert a.size == NPOP * ny * nx
+        if a.size != NPOP * ny * nx:
+            raise ValueError("populations: need %d values, got %d"
+                             % (NPOP * ny * nx, a.size))
         self._check(self._lib.lbm_set_fields(self._h, k, FIELD_POPS,
                                              a.ctypes.data, a.nbytes))
 

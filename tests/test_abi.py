@@ -54,6 +54,23 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lbm_obs_size == 144
 
 
+def test_binding_rejects_mismatched_arrays_without_touching_the_gpu(lib):
+    # the library reads ny * nx values from each field: the binding checks
+    # the shapes before it calls create
+    from paper_1309_6726_gb300 import inputs as I, lbm
+    geom, mp, _ = I.config_small()
+    bad = I.Geometry(geom.solid, geom.rho_a[:, :-1], geom.rho_b, geom.conc,
+                     geom.cap_x0, geom.cap_x1)
+    with pytest.raises(ValueError, match="rho_a"):
+        lbm.Solver(bad, mp)
+    flat = I.Geometry(geom.solid.ravel(), geom.rho_a, geom.rho_b, geom.conc,
+                      geom.cap_x0, geom.cap_x1)
+    with pytest.raises(ValueError, match="solid"):
+        lbm.Solver(flat, mp)
+    with pytest.raises(ValueError):
+        lbm.Solver([geom, geom], [mp])
+
+
 def test_fit_reff_host_helper(lib):
     # Host-only arithmetic: a front at exactly the Eq. 1 speed for height H
     # gives r_eff = H / 2.
