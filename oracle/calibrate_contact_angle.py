@@ -6,7 +6,9 @@ two menisci relax, and measures theta from a circle fitted to the meniscus
 (``analysis.meniscus_cos_theta``).  The paper fixes the contact angle of
 molten Si on carbon at 30 degrees (Sec. I) and adjusts the adhesive force to
 reproduce it; this script produces the (theta, g) table that the input
-generator interpolates.  It calls only the oracle.
+generator interpolates.  It calls only the oracle.  Test infrastructure
+like the rest of this package: the product path never runs it; only its
+output table, committed beside the input generator, is used.
 
 Usage: python -m oracle.calibrate_contact_angle
 """
