@@ -2,7 +2,7 @@
 other pin uses: a shear wave decays at the kinematic viscosity
 nu = (tau - 1/2) / 3, and a standing density wave oscillates at the lattice
 sound speed c_s = 1 / sqrt(3) (the isotropic pressure rho / 3 of the
-equilibrium).  Both components carry half of the fluid with no cohesion,
+equilibrium); and the D2Q4 solute moves with the fluid.  Both components carry half of the fluid with no cohesion,
 so together they are one BGK fluid (Sec. II model with G_c = 0)."""
 import math
 
@@ -76,3 +76,28 @@ def test_standing_density_wave_oscillates_at_the_sound_speed():
     t0 = i - 1 + amps[i - 1] / (amps[i - 1] - amps[i])
     c_s = math.pi / (2 * k * t0)
     assert c_s == pytest.approx(1 / math.sqrt(3), rel=1e-2)
+
+
+def test_solute_blob_moves_with_the_fluid():
+    # reading c7: g_eq = (C/4)(1 + 2 e.u) carries C u, so in a uniform flow
+    # a solute blob's centre of mass moves u per step (and its mass stays)
+    # wide enough that the diffusing blob (sigma about 9 lu at the end)
+    # never reaches the periodic seam, where the centroid would wrap
+    nx, ny, steps = 200, 3, 200
+    u = (0.05, 0.0)
+    ones = np.ones((ny, nx))
+    lat = _fluid(nx, ny, 1.0, ones, u[0] * ones, u[1] * ones)
+    x = np.arange(nx)[None, :].astype(float) * np.ones((ny, 1))
+    c0 = np.exp(-((x - 80.0) / 6.0) ** 2)
+    g = np.zeros((4, ny, nx))
+    for yy in range(ny):
+        for xx in range(nx):
+            g[:, yy, xx] = OL.geq(c0[yy, xx], u[0], u[1])
+    lat.set_solute(g)
+    lat.step(steps)
+    c = lat.concentration()
+    assert c.sum() == pytest.approx(c0.sum(), rel=1e-12)
+    shift = (c * x).sum() / c.sum() - (c0 * x).sum() / c0.sum()
+    # exact up to rounding: the collision keeps the flux C u of the
+    # equilibrium, so the first moment advances by C u every step
+    assert shift == pytest.approx(u[0] * steps, rel=1e-10)
