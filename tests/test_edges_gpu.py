@@ -6,6 +6,7 @@ against the FP64 oracle.
   kernel, FP16 headline and FP32 comparison): three capillaries sampled
   from it (smallest, median and largest) are advanced by the oracle alone
   and compared element by element.
+* The 2048 x 2048 disc preform at its full size, both storages.
 * Degenerate rates: k_r = 0 (no deposit, the mask never changes) and a
   vanishing threshold (every reacting node turns solid at once, growth
   cascades one layer per step) -- masks exact against the oracle.
@@ -51,6 +52,23 @@ def test_full_sweep_sampled_capillaries(precision, tol):
         np.testing.assert_array_equal(s.solid_mask(k), o.solid())
         assert pop_error(s.populations(k), oracle_pops(o)) < tol, k
     s.close()
+
+
+def test_full_size_preform_both_storages():
+    # One 2048 x 2048 lattice (4.2e6 nodes, its tall tile columns cut into
+    # strips over every block, walls around thousands of discs) for three
+    # steps, element by element against the oracle in both storages.  No
+    # node reacts this early (no disc touches the reservoir); growth on a
+    # preform is compared on the 192 x 192 one.
+    geom, mp, _ = I.config_preform()
+    o = oracle_for(geom, mp)
+    o.step(3)
+    fo = oracle_pops(o)
+    for precision, tol in (("fp32", FP32_TOL), ("fp16", FP16_TOL_SHORT)):
+        with lbm.Solver(geom, mp, precision) as s:
+            s.step(3)
+            np.testing.assert_array_equal(s.solid_mask(), o.solid())
+            assert pop_error(s.populations(), fo) < tol, precision
 
 
 def _capillary(k_r, m_threshold, nx=96, ny=14):
