@@ -2,16 +2,38 @@
 the same seeded inputs.
 
 Tolerances.  The kernels compute in FP32 and store FP32 (or FP16
-deviations); the oracle computes in FP64.  A population's error is stated
-relative to its lattice weight times a reference density of 1 (the
-majority phase).  FP32: 1e-5, also over the 2000 steps of the small
-capillary, where the moving meniscus integrates FP32 rounding: the
-textbook formulas evaluated in FP32 drift to 6e-5 there
-(test_fp32_bound.py); the kernels' pairwise equilibrium and rest-population
-mass closure stay near 6e-6.  FP16 storage: a measured bound,
-stated with its test.  Integer and index results -- the solid mask, the
-step a node turns solid, the pore-closure step -- must match exactly; the
-front position within 0.5 lattice units.
+deviations); the oracle computes in FP64.  Two measures of a population's
+error are checked side by side:
+
+* of the weight: |f_gpu - f_oracle| / w_i, i.e. relative to a population
+  of the majority phase (density 1).  FP32: 1e-5, also over the 2000 steps
+  of the small capillary, where the moving meniscus integrates FP32
+  rounding: the textbook formulas evaluated in FP32 drift to 6e-5 there
+  (test_fp32_bound.py); the kernels' pairwise equilibrium and
+  rest-population mass closure stay near 6e-6.
+* per component: |f_gpu - f_oracle| / (w_i rho_sigma(x)) with the
+  component's own oracle density at the node (C for the solute), over the
+  nodes where that density is at least 1e-3 (gpu_helpers.pop_rel_error),
+  so the minority phase (density 0.006) and dilute solute are held to
+  their own size.  FP32: 1e-4.  The bound the weight-normalised measure
+  meets (1e-5) is out of reach here for FP32 arithmetic itself: where a
+  component is the minority next to a sharp interface its Shan-Chen shift
+  tau F / rho is of order one (it does not scale with its own density),
+  the equilibrium's terms 3 e.u and 9/2 (e.u)^2 are then of order ten and
+  largely cancel, and their FP32 rounding is 1e-5 of w_i rho_sigma and
+  more.  Measured: the oracle's own formulas compiled in FP32 reach
+  1.1e-5 after one step of the random states and 1.8e-5 after ten steps
+  of a sweep capillary; the kernels reach 4.6e-5 on the random states
+  (with growth), 2.7e-5 on the sweep sample, and 6.3e-5 after the 2000
+  steps of the small capillary, where the FP32-compiled oracle reaches
+  6.4e-4 (the minority's relative error follows the majority's absolute
+  error through the cohesion force).  A one-off perturbation of 2^-24
+  does not grow (5e-7 after 2000 steps): the growth is accumulated
+  rounding, not instability.
+
+FP16 storage: measured bounds, stated with their tests.  Integer and index
+results -- the solid mask, the step a node turns solid, the pore-closure
+step -- must match exactly; the front position within 0.5 lattice units.
 """
 
 import numpy as np
@@ -20,11 +42,13 @@ import pytest
 from oracle import analysis as A
 from paper_1309_6726_gb300 import inputs as I
 from paper_1309_6726_gb300 import lbm
-from tests.gpu_helpers import oracle_for, oracle_pops, pop_error
+from tests.gpu_helpers import assert_rel, oracle_for, oracle_pops, pop_error
 
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
+#: per-component relative bound (see the module docstring)
+FP32_REL = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +88,9 @@ def test_random_state_steps(nx, ny, seed):
         s.step(n)
         o.step(n)
         np.testing.assert_array_equal(s.solid_mask(), o.solid())
-        assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+        fg, fo = s.populations(), oracle_pops(o)
+        assert pop_error(fg, fo) < FP32_TOL
+        assert_rel(fg, fo, FP32_REL)
         np.testing.assert_allclose(s.deposit(), o.deposit(), rtol=1e-6,
                                    atol=1e-7)
         go = s.observables()[0]
@@ -93,8 +119,11 @@ def test_small_capillary_2000_steps():
         else:
             assert abs(go["front"] - oo["front"]) < 0.5
         assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+        assert_rel(s.populations(), oracle_pops(o), FP32_REL)
     err = pop_error(s.populations(), oracle_pops(o))
-    print("small capillary: max population error / w_i = %.3g" % err)
+    rel = assert_rel(s.populations(), oracle_pops(o), FP32_REL)
+    print("small capillary: max population error / w_i = %.3g, per "
+          "component %s" % (err, rel))
     go = s.observables()[0]
     oo = A.lattice_observables(o)
     assert go["closure_step"] == o.closure_step
@@ -125,6 +154,7 @@ def test_batch_matches_independent_lattices():
     for k, (g, o) in enumerate(zip(geoms, ors)):
         np.testing.assert_array_equal(s.solid_mask(k), o.solid())
         assert pop_error(s.populations(k), oracle_pops(o)) < FP32_TOL
+        assert_rel(s.populations(k), oracle_pops(o), FP32_REL)
         oo = A.lattice_observables(o)
         assert obs[k]["closure_step"] == o.closure_step
         assert obs[k]["delta_e"] == oo["delta_e"]
@@ -160,6 +190,7 @@ def test_paper_scale_capillary_full_size():
     o.step(12)
     np.testing.assert_array_equal(s.solid_mask(), o.solid())
     assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
+    assert_rel(s.populations(), oracle_pops(o), FP32_REL)
     assert (o.solid() != geom.solid).sum() > 0
 
 
@@ -309,6 +340,7 @@ def test_preform_small_fp32_and_fp16():
         fo = oracle_pops(o)
         assert pop_error(s32.populations(), fo) < FP32_TOL
         assert pop_error(s16.populations(), fo) < FP16_TOL_LONG
+        assert_rel(s32.populations(), fo, FP32_REL)
     assert (o.solid() != geom.solid).sum() > 0
     g32 = s32.observables()[0]
     led = o.ledger()
