@@ -35,12 +35,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated error"
 
-#: algorithmic bytes per fluid-node update of the step kernel: each stored
-#: element read once and written once, the mask byte read once.
-#: FP32: 22 populations x 4 B x 2 = 176, + 1 mask byte.
-#: FP16: 20 deviations x 2 B x 2 = 80, 5 references x 2 B x 2 = 20,
-#: 2 FP32 rest populations x 4 B x 2 = 16, + 1.
-BYTES_PER_NODE = {"fp32": 177.0, "fp16": 117.0}
+#: algorithmic bytes per fluid-node update: each of the 22 populations (18
+#: D2Q9, 4 D2Q4) read once and written once at the storage precision, the
+#: mask byte read once -- FP32: 22 x 4 B x 2 + 1 = 177; 16-bit storage:
+#: 22 x 2 B x 2 + 1 = 89.  The roofline's `achieved` uses these.
+BYTES_PER_NODE = {"fp32": 177.0, "fp16": 89.0}
+#: bytes the layout actually stores and reloads per fluid-node update
+#: (reported beside the algorithmic count): FP16 keeps 20 deviations
+#: (80 B read + written), 5 FP16 references (20 B) and 2 FP32 rest
+#: populations (16 B), + 1 mask byte.
+STORED_BYTES_PER_NODE = {"fp32": 177.0, "fp16": 117.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel
@@ -384,6 +388,7 @@ def main():
             and per_node is not None):
         traffic = per_node * n_fluid
     bpn = BYTES_PER_NODE[args.precision] + DEPOSIT_BYTES * f_s
+    stored = STORED_BYTES_PER_NODE[args.precision] + DEPOSIT_BYTES * f_s
     achieved = n_fluid * bpn / (ms_step / 1e3) / 1e9
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
@@ -414,6 +419,10 @@ def main():
                          "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "bytes_per_fluid_node": bpn,
+                         "stored_bytes_per_fluid_node": stored,
+                         "traffic_over_algorithmic":
+                             None if traffic is None
+                             else traffic / (n_fluid * bpn),
                          "kernel": "k_step_tma (one launch per step)"},
             "compare": compare,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

@@ -55,6 +55,10 @@ def test_gpu_arm_line_small_batch():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] > 0 and r["peak"] > 0
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
+    # achieved counts the algorithmic bytes (16-bit storage: 89 B per fluid
+    # node plus 16 B per surface node), not the layout's own
+    assert 89.0 <= r["bytes_per_fluid_node"] < 89.0 + 16.0
+    assert r["stored_bytes_per_fluid_node"] >= r["bytes_per_fluid_node"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
     e = d["e2e"]
