@@ -63,12 +63,14 @@ typedef enum {
  * the deposit and the growth test are FP64 in both. */
 typedef enum {
     LBM_FP32 = 0, /* populations stored as FP32 */
-    LBM_FP16 = 1  /* moving populations and solute stored as FP16
-                     deviations from per-node FP16 references (w_1 rho~ and
-                     w_5 rho~ per component with rho~ = f_0 / w_0, C / 4 for
-                     the solute); the rest populations stay FP32 and take up
-                     the rounding of the moving ones, so each node keeps its
-                     mass to FP32 rounding */
+    LBM_FP16 = 1  /* populations stored as FP16 deviations from per-node
+                     FP32 references: f_i / w_i - rho~ per component (rho~
+                     = f_0 / w_0, the rest population, stored in FP32) and
+                     4 g_k - C~ for the solute, scaled by 2^10, the A and B
+                     deviations of a direction packed in one 32-bit word;
+                     the references take up the rounding of the deviations,
+                     so each node keeps its mass to FP32 rounding.  13
+                     32-bit words per node against FP32's 22. */
 } lbm_precision;
 
 /* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,

@@ -21,27 +21,23 @@ namespace lbmk {
 cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
                                int ty, bool half, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
-                            const CUtensorMap *mom_maps,
-                            const CUtensorMap *rest_maps,
                             const CUtensorMap *mask_maps,
-                            const CUtensorMap *out_maps,
-                            const CUtensorMap *out_mom_maps,
-                            const CUtensorMap *out_rest_maps,
-                            const TileRec *sched, int nslots, int grid, int tx,
-                            int ty, bool half, int *err, cudaStream_t s);
+                            const CUtensorMap *out_maps, const TileRec *sched,
+                            int nslots, int grid, int tx, int ty, bool half,
+                            int *err, cudaStream_t s);
 cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
-int tma_box_x(int tx, bool half);
+int tma_box_x(int tx);
 int tma_mask_box_x(int tx);
 __global__ void k_rest_state(const LatDesc *, int, const float *,
                              const float *, const float *, const uint8_t *,
                              float *);
 __global__ void k_unstream(const LatDesc *, int, const float *,
-                           const uint8_t *, uint8_t, void *, __half *, bool);
-__global__ void k_export(const LatDesc *, int, const void *, const __half *,
-                         const uint8_t *, const double *, long long, bool,
-                         float *, float *, double *);
-__global__ void k_settle(const LatDesc *, int, const void *, const __half *,
-                         uint8_t *, double *, LatState *, long long, bool);
+                           const uint8_t *, uint8_t, void *, bool);
+__global__ void k_export(const LatDesc *, int, const void *, const uint8_t *,
+                         const double *, long long, bool, float *, float *,
+                         double *);
+__global__ void k_settle(const LatDesc *, int, const void *, uint8_t *,
+                         double *, LatState *, long long, bool);
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
 __global__ void k_solid_mask(const LatDesc *, int, const uint8_t *, uint8_t,
                              uint8_t *);
@@ -50,8 +46,8 @@ __global__ void k_col_init(const LatDesc *, int, const uint8_t *, int32_t *,
                            int16_t *, LatState *);
 __global__ void k_obs_columns(const LatDesc *, const int32_t *,
                               const int64_t *, int, const void *,
-                              const __half *, const uint8_t *,
-                              const double *, long long, bool, ColObs *);
+                              const uint8_t *, const double *, long long,
+                              bool, ColObs *);
 struct LbmObsDev;
 __global__ void k_obs_reduce(const LatDesc *, const int64_t *,
                              const ColObs *, const int16_t *,
@@ -74,7 +70,7 @@ struct lbm_handle {
     int64_t ncols = 0;               // columns of all lattices
     int64_t nsec = 0;                // section columns of all lattices
     int ntiles = 0;
-    int64_t pop_elems = 0, mom_elems = 0, node_elems = 0;
+    int64_t pop_elems = 0, node_elems = 0;  // 32-bit words, mask bytes
     size_t max_nodes = 0;            // largest nx*ny
     // device
     LatDesc *d_desc = nullptr;
@@ -82,7 +78,6 @@ struct lbm_handle {
     int32_t *d_col_lat = nullptr;
     int64_t *d_col_base = nullptr;
     void *d_pop[2] = {nullptr, nullptr};
-    __half *d_mom[2] = {nullptr, nullptr};
     uint8_t *d_mask = nullptr;
     double *d_m = nullptr;
     int32_t *d_col_fluid = nullptr;
@@ -95,11 +90,10 @@ struct lbm_handle {
     float *d_canon = nullptr;      // [22][ny][nx] scratch of one lattice
     float *d_dens = nullptr;       // [3][ny][nx]
     double *d_dep = nullptr;       // [ny][nx]
-    // [2 buffers][count] population (FP16 moment) maps over the ghost band
-    // for the tile copies, then [2 buffers][count] over the lattice itself
-    // for the output stores
+    // [2 buffers][count] population maps over the ghost band for the tile
+    // copies, then [2 buffers][count] over the lattice itself for the
+    // output stores
     CUtensorMap *d_maps = nullptr;
-    CUtensorMap *d_mom_maps = nullptr;
     CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
     TileRec *d_sched = nullptr;        // TMA kernel: tiles of each block
     int sched_grid = 0, sched_slots = 0;
@@ -141,10 +135,10 @@ static cudaError_t dalloc(T **p, size_t n) {
 
 static void free_all(lbm_handle *h) {
     void *ps[] = {h->d_desc, h->d_tile_lat, h->d_col_lat, h->d_col_base,
-                  h->d_pop[0], h->d_pop[1], h->d_mom[0], h->d_mom[1],
+                  h->d_pop[0], h->d_pop[1],
                   h->d_mask, h->d_m, h->d_col_fluid, h->d_wall0, h->d_st,
                   h->d_step, h->d_done, h->d_cols, h->d_obs, h->d_canon,
-                  h->d_dens, h->d_dep, h->d_maps, h->d_mom_maps, h->d_mask_maps, h->d_err,
+                  h->d_dens, h->d_dep, h->d_maps, h->d_mask_maps, h->d_err,
                   h->d_sched};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -219,9 +213,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// One 3-D tensor map per lattice and buffer: (x, y, plane) over the lattice
-// (x < nx, y < ny: coordinates beyond read as zeros), box = the kernel's
-// tile plus halo, all planes.
+// One 3-D tensor map per lattice and buffer: (x, y, plane) over the
+// lattice's planes of 32-bit words including the ghost band (box = the
+// kernel's tile plus halo, all planes), and one over the lattice's own nodes
+// (box = the tile) for the output stores; coordinates beyond read as zeros.
 static bool make_maps(lbm_handle *h, std::string &why) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) {
@@ -229,20 +224,17 @@ static bool make_maps(lbm_handle *h, std::string &why) {
         return false;
     }
     const int count = h->count;
-    const size_t esz = h->half ? 2 : 4;
-    // moms: [2 buffers][count] reference copies, [2][count] reference
-    // stores, [2][count] rest-plane copies, [2][count] rest-plane stores
-    std::vector<CUtensorMap> maps(4 * count), moms(8 * count);
-    const cuuint64_t npl = h->half ? NP16 : NPOP;
-    const CUtensorMapDataType pty =
-        h->half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const size_t esz = 4;
+    std::vector<CUtensorMap> maps(4 * count);
+    const cuuint64_t npl = h->half ? NW16 : NPOP;
+    const CUtensorMapDataType pty = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int b = 0; b < 2; ++b) {
         for (int l = 0; l < count; ++l) {
             const LatDesc &d = h->desc[l];
             const cuuint64_t rows = (cuuint64_t)(d.ny + 2 * GHOST);
             cuuint64_t dims[3] = {(cuuint64_t)d.pitch, rows, npl};
             cuuint64_t strides[2] = {(cuuint64_t)d.pitch * esz, (cuuint64_t)d.plane * esz};
-            cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx, h->half),
+            cuuint32_t box[3] = {(cuuint32_t)tma_box_x(h->tx),
                                  (cuuint32_t)(h->ty + 4), (cuuint32_t)npl};
             cuuint32_t es[3] = {1, 1, 1};
             void *base = (char *)h->d_pop[b] +
@@ -257,22 +249,6 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                       std::to_string((int)r);
                 return false;
             }
-            if (h->half) {
-                cuuint64_t mdims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NMOM};
-                cuuint32_t mbox[3] = {box[0], box[1], (cuuint32_t)NMOM};
-                void *mbase = (char *)h->d_mom[b] +
-                              (size_t)(d.mom_off - GHOST * d.pitch - XGHOST) * 2;
-                r = enc(&moms[b * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                        mbase, mdims, strides, mbox, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) {
-                    why = "cuTensorMapEncodeTiled failed for moments, code " +
-                          std::to_string((int)r);
-                    return false;
-                }
-            }
             // output: the lattice's own nodes, logical (0, 0) at the base
             // (16-byte aligned: the ghost band is 16 columns wide)
             cuuint64_t odims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, npl};
@@ -285,44 +261,6 @@ static bool make_maps(lbm_handle *h, std::string &why) {
                 why = "cuTensorMapEncodeTiled failed for the output, code " +
                       std::to_string((int)r);
                 return false;
-            }
-            if (h->half) {
-                cuuint64_t mdims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NMOM};
-                cuuint32_t mbox[3] = {obox[0], obox[1], (cuuint32_t)NMOM};
-                r = enc(&moms[(2 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                        (char *)h->d_mom[b] + (size_t)d.mom_off * 2, mdims, strides,
-                        mbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) {
-                    why = "cuTensorMapEncodeTiled failed for the moment output, code " +
-                          std::to_string((int)r);
-                    return false;
-                }
-                // FP32 rest planes after the 5 reference planes of the block
-                const int64_t g0 = (int64_t)GHOST * d.pitch + XGHOST;
-                char *rbase = (char *)h->d_mom[b] +
-                              (size_t)((d.mom_off - g0) + NMOM * d.plane) * 2;
-                cuuint64_t rstr[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane * 4};
-                cuuint64_t rdims[3] = {(cuuint64_t)d.pitch, rows, (cuuint64_t)NREST};
-                cuuint32_t rbox[3] = {box[0], box[1], (cuuint32_t)NREST};
-                r = enc(&moms[(4 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                        rbase, rdims, rstr, rbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                cuuint64_t rodims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)NREST};
-                cuuint32_t robox[3] = {obox[0], obox[1], (cuuint32_t)NREST};
-                if (r == CUDA_SUCCESS)
-                    r = enc(&moms[(6 + b) * count + l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                            rbase + (size_t)g0 * 4, rodims, rstr, robox, es,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) {
-                    why = "cuTensorMapEncodeTiled failed for the rest planes, code " +
-                          std::to_string((int)r);
-                    return false;
-                }
             }
         }
     }
@@ -354,13 +292,6 @@ static bool make_maps(lbm_handle *h, std::string &why) {
     if (cudaMalloc(&h->d_maps, maps.size() * sizeof(CUtensorMap)) != cudaSuccess ||
         cudaMemcpy(h->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
-        why = "tensor map upload";
-        return false;
-    }
-    if (h->half &&
-        (cudaMalloc(&h->d_mom_maps, moms.size() * sizeof(CUtensorMap)) != cudaSuccess ||
-         cudaMemcpy(h->d_mom_maps, moms.data(), moms.size() * sizeof(CUtensorMap),
-                    cudaMemcpyHostToDevice) != cudaSuccess)) {
         why = "tensor map upload";
         return false;
     }
@@ -473,7 +404,7 @@ static lbm_status retile(lbm_handle *h, bool tma, int tx, int ty) {
     CK(h, cudaMemcpy(h->d_desc, h->desc.data(), h->count * sizeof(LatDesc),
                      cudaMemcpyHostToDevice));
     h->ntiles = tiles;
-    for (CUtensorMap **m : {&h->d_maps, &h->d_mom_maps, &h->d_mask_maps}) {
+    for (CUtensorMap **m : {&h->d_maps, &h->d_mask_maps}) {
         if (*m) cudaFree(*m);
         *m = nullptr;
     }
@@ -524,7 +455,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     // ---- packed ragged layout ------------------------------------------
     h->desc.resize(count);
     h->col_base.resize(count);
-    int64_t pop = 0, mom = 0, node = 0, cols = 0, sec = 0;
+    int64_t pop = 0, node = 0, cols = 0, sec = 0;
     int tiles = 0;
     for (int l = 0; l < count; ++l) {
         const lbm_geometry &G = g[l];
@@ -543,11 +474,10 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.plane = (int64_t)(d.ny + 2 * GHOST) * d.pitch;
         d.node_off = node + GHOST * d.pitch + XGHOST;
         d.pop_off = pop + GHOST * d.pitch + XGHOST;
-        d.mom_off = mom + GHOST * d.pitch + XGHOST;
+        d.pad64_ = 0;
         d.col_off = sec;
         node += d.plane;
-        pop += (h->half ? NP16 : NPOP) * d.plane;
-        mom += MOM_BLOCK * d.plane;
+        pop += (h->half ? NW16 : NPOP) * d.plane;
         h->col_base[l] = cols;
         cols += d.nx;
         sec += G.cap_x1 - G.cap_x0;
@@ -568,7 +498,6 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     }
     h->ntiles = tiles;
     h->pop_elems = pop;
-    h->mom_elems = mom;
     h->node_elems = node;
     h->ncols = cols;
     h->nsec = sec;
@@ -585,7 +514,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     // k_col_init) below
 
     // ---- device allocations ----------------------------------------------
-    const size_t esz = h->half ? sizeof(__half) : sizeof(float);
+    const size_t esz = 4;  // 32-bit words in both storages
     cudaError_t e = cudaSuccess;
 #define AL(ptr, n)                                                      \
     if (e == cudaSuccess) e = dalloc(&(ptr), (n));
@@ -595,10 +524,6 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     AL(h->d_col_base, count);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[0], pop * esz);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[1], pop * esz);
-    if (h->half) {
-        AL(h->d_mom[0], mom);
-        AL(h->d_mom[1], mom);
-    }
     AL(h->d_mask, node);
     AL(h->d_m, node);
     AL(h->d_col_fluid, sec);
@@ -637,10 +562,6 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     bad(cudaMemset(h->d_mask, 0, node), "memset");
     bad(cudaMemset(h->d_pop[0], 0, pop * esz), "memset");
     bad(cudaMemset(h->d_pop[1], 0, pop * esz), "memset");
-    if (h->half) {
-        bad(cudaMemset(h->d_mom[0], 0, mom * sizeof(__half)), "memset");
-        bad(cudaMemset(h->d_mom[1], 0, mom * sizeof(__half)), "memset");
-    }
     bad(cudaMemset(h->d_m, 0, node * sizeof(double)), "memset");
     std::vector<LatState> st0(count);
     for (auto &x : st0) {
@@ -684,7 +605,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
                 h->d_desc, l, tsol, h->d_col_fluid, h->d_wall0, h->d_st);
         dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
         k_rest_state<<<grid, blk, 0, s>>>(h->d_desc, l, tmp, tmp + N, tmp + 2 * N, tsol, h->d_canon);
-        k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->d_mom[0], h->half);
+        k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->half);
         bad(cudaGetLastError(), "init kernels");
     }
     bad(cudaStreamSynchronize(s), "init sync");
@@ -733,8 +654,6 @@ static StepArgs step_args(lbm_handle *h) {
     a.tile_lat = h->d_tile_lat;
     a.fin = h->d_pop[h->cur];
     a.fout = h->d_pop[h->cur ^ 1];
-    a.min_ = h->d_mom[h->cur];
-    a.mout = h->d_mom[h->cur ^ 1];
     a.mask = h->d_mask;
     a.m = h->d_m;
     a.col_fluid = h->d_col_fluid;
@@ -748,13 +667,10 @@ static StepArgs step_args(lbm_handle *h) {
 // One launch of the TMA step kernel reading buffer cur, writing cur ^ 1.
 static cudaError_t launch_tma(lbm_handle *h) {
     const int c = h->count, in = h->cur, out = h->cur ^ 1;
-    const CUtensorMap *m = h->d_mom_maps;  // see make_maps for its blocks
-    return launch_step_tma(
-        step_args(h), h->d_maps + in * c, h->half ? m + in * c : nullptr,
-        h->half ? m + (4 + in) * c : nullptr, h->d_mask_maps,
-        h->d_maps + (2 + out) * c, h->half ? m + (2 + out) * c : nullptr,
-        h->half ? m + (6 + out) * c : nullptr, h->d_sched, h->sched_slots,
-        h->sched_grid, h->tx, h->ty, h->half, h->d_err, h->stream);
+    return launch_step_tma(step_args(h), h->d_maps + in * c, h->d_mask_maps,
+                           h->d_maps + (2 + out) * c, h->d_sched, h->sched_slots,
+                           h->sched_grid, h->tx, h->ty, h->half, h->d_err,
+                           h->stream);
 }
 
 static cudaError_t launch_one(lbm_handle *h) {
@@ -834,7 +750,7 @@ extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
     const int nb = (int)((h->ncols + 31) / 32);
     k_obs_columns<<<nb, dim3(32, OBS_ROWS), 0, h->stream>>>(
         h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
-        h->d_mom[h->cur], h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
+        h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
     k_obs_reduce<<<h->count, 256, 0, h->stream>>>(
         h->d_desc, h->d_col_base, h->d_cols, h->d_wall0, h->d_st, h->steps,
         (LbmObsDev *)h->d_obs);
@@ -884,8 +800,7 @@ extern "C" lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
     if (bytes != need) return fail(h, LBM_EINVAL, "size mismatch");
     dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
     k_export<<<grid, blk, 0, h->stream>>>(
-        h->d_desc, k, h->d_pop[h->cur], h->d_mom[h->cur], h->d_mask, h->d_m,
-        h->steps, h->half, which == LBM_FIELD_POPS ? h->d_canon : nullptr,
+        h->d_desc, k, h->d_pop[h->cur], h->d_mask, h->d_m, h->steps, h->half, which == LBM_FIELD_POPS ? h->d_canon : nullptr,
         which == LBM_FIELD_DENSITY ? h->d_dens : nullptr,
         which == LBM_FIELD_DEPOSIT ? h->d_dep : nullptr);
     CK(h, cudaGetLastError());
@@ -902,8 +817,8 @@ static lbm_status settle(lbm_handle *h, int k) {
     const LatDesc &d = h->desc[k];
     dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
     k_settle<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_pop[h->cur],
-                                         h->d_mom[h->cur], h->d_mask, h->d_m,
-                                         h->d_st, h->steps, h->half);
+                                         h->d_mask, h->d_m, h->d_st, h->steps,
+                                         h->half);
     k_mask_agree<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_mask, h->steps);
     CK(h, cudaGetLastError());
     return LBM_OK;
@@ -924,7 +839,7 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
         const MaskBits mb(h->steps);
         k_unstream<<<grid, blk, 0, h->stream>>>(h->d_desc, k, h->d_canon, h->d_mask,
                                                mb.force, h->d_pop[h->cur],
-                                               h->d_mom[h->cur], h->half);
+                                               h->half);
         CK(h, cudaGetLastError());
         CK(h, cudaStreamSynchronize(h->stream));
         return LBM_OK;
@@ -961,12 +876,12 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
 
 // ---- checkpoints -----------------------------------------------------------
 
-static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '3'};
+static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '4'};
 
 struct CkptHeader {
     char magic[8];
     int32_t count, half;
-    int64_t pop_elems, mom_elems, node_elems, nsec, steps;
+    int64_t pop_elems, node_elems, nsec, steps;
     int32_t cur, pad;
 };
 
@@ -974,13 +889,12 @@ extern "C" lbm_status lbm_save(lbm_handle *h, const char *path) {
     if (!h || !path) return fail(h, LBM_EINVAL, "NULL argument");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     CK(h, cudaStreamSynchronize(h->stream));
-    const size_t esz = h->half ? 2 : 4;
+    const size_t esz = 4;
     CkptHeader hd;
     memcpy(hd.magic, kMagic, 8);
     hd.count = h->count;
     hd.half = h->half;
     hd.pop_elems = h->pop_elems;
-    hd.mom_elems = h->half ? h->mom_elems : 0;
     hd.node_elems = h->node_elems;
     hd.nsec = h->nsec;
     hd.steps = h->steps;
@@ -1005,7 +919,6 @@ extern "C" lbm_status lbm_save(lbm_handle *h, const char *path) {
         }
     };
     dump(h->d_pop[h->cur], h->pop_elems * esz);
-    if (h->half) dump(h->d_mom[h->cur], h->mom_elems * 2);
     dump(h->d_mask, h->node_elems);
     dump(h->d_m, h->node_elems * 8);
     dump(h->d_col_fluid, h->nsec * 4);
@@ -1037,7 +950,7 @@ extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
         fclose(f);
         return fail(h, LBM_EINVAL, "checkpoint does not match this handle");
     }
-    const size_t esz = h->half ? 2 : 4;
+    const size_t esz = 4;
     auto slurp = [&](void *dptr, size_t bytes) {
         if (!ok) return;
         std::vector<uint8_t> buf(std::min<size_t>(bytes, (size_t)1 << 28));
@@ -1052,7 +965,6 @@ extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
     };
     h->cur = 0;
     slurp(h->d_pop[0], h->pop_elems * esz);
-    if (h->half) slurp(h->d_mom[0], h->mom_elems * 2);
     slurp(h->d_mask, h->node_elems);
     slurp(h->d_m, h->node_elems * 8);
     slurp(h->d_col_fluid, h->nsec * 4);
@@ -1124,7 +1036,7 @@ extern "C" lbm_status lbm_autotune(lbm_handle *h, int32_t steps,
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     CK(h, cudaStreamSynchronize(h->stream));
     // snapshot of everything a step changes
-    const size_t esz = h->half ? 2 : 4;
+    const size_t esz = 4;
     struct Piece { void *dev; size_t bytes; };
     const int cur0 = h->cur;
     const int64_t steps0 = h->steps;
@@ -1135,7 +1047,6 @@ extern "C" lbm_status lbm_autotune(lbm_handle *h, int32_t steps,
         {h->d_col_fluid, (size_t)h->nsec * 4},
         {h->d_st, (size_t)h->count * sizeof(LatState)},
         {h->d_step, 8}};
-    if (h->half) parts.push_back({h->d_mom[cur0], (size_t)h->mom_elems * 2});
     size_t total = 0;
     for (auto &p : parts) total += (p.bytes + 255) / 256 * 256;
     char *snap = nullptr;

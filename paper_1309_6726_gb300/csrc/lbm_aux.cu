@@ -12,24 +12,29 @@
 
 namespace lbmk {
 
-__device__ __forceinline__ float load_pop(const void *base, const __half *mom,
-                                          const LatDesc &d, bool half, int q,
-                                          int64_t e) {
+// Stored value q (0..21: A, B, solute) of node offset e, in the
+// populations' own units (FP16 storage: read back and unscaled).
+__device__ __forceinline__ float load_pop(const void *base, const LatDesc &d,
+                                          bool half, int q, int64_t e) {
     if (!half) return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
-    if (q == 0 || q == Q)  // rest populations: FP32, in the moment block
-        return rest_planes(mom, d)[(q == Q ? d.plane : 0) + e];
-    const float dv =
-        __half2float(static_cast<const __half *>(base)[d.pop_off + sp16(q) * d.plane + e]);
-    const int comp = q < Q ? 0 : (q < 2 * Q ? 1 : 2);
-    if (comp == 2) return dec_sol(dv, __half2float(mom[d.mom_off + kSolRef * d.plane + e]));
-    const int i = q - comp * Q;
-    return dec_pop(i, dv, __half2float(mom[d.mom_off + refp(comp, i) * d.plane + e]));
+    const uint32_t *w = static_cast<const uint32_t *>(base) + d.pop_off;
+    const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
+    if (q < 2 * Q) {
+        const int comp = q < Q ? 0 : 1, i = q - comp * Q;
+        const float r = ref[comp * d.plane + e];
+        if (i == 0) return wq(0) * r;
+        const float2 dv = __half22float2(bits_h2(w[(i - 1) * d.plane + e]));
+        return wq(i) * dec16(comp ? dv.y : dv.x, r);
+    }
+    const int k = q - 2 * Q;
+    return 0.25f * dec_sol16(w[(W16_SOL + (k >> 1)) * d.plane + e], k,
+                             ref[2 * d.plane + e]);
 }
 
 // Post-streaming populations of node (x, y) at the current step: 22 values
 // (A, B, solute), pulled from the stored post-collision state with the
 // streaming mask bit.
-__device__ __forceinline__ void pull_node(const void *fin, const __half *mom,
+__device__ __forceinline__ void pull_node(const void *fin,
                                           const uint8_t *mask,
                                           const LatDesc &d, bool half,
                                           uint8_t pullbit, int x, int y,
@@ -40,29 +45,38 @@ __device__ __forceinline__ void pull_node(const void *fin, const __half *mom,
         const int xs = wrap1(x - cx(i), nx), ys = wrap1(y - cy(i), ny);
         const int64_t src = (int64_t)ys * d.pitch + xs;
         const bool b = i != 0 && (mask[src] & pullbit);
-        out[i] = load_pop(fin, mom, d, half, b ? opp(i) : i, b ? own : src);
-        out[Q + i] = load_pop(fin, mom, d, half, Q + (b ? opp(i) : i), b ? own : src);
+        out[i] = load_pop(fin, d, half, b ? opp(i) : i, b ? own : src);
+        out[Q + i] = load_pop(fin, d, half, Q + (b ? opp(i) : i), b ? own : src);
     }
     for (int k = 0; k < QS; ++k) {
         const int xs = wrap1(x - sx(k), nx), ys = wrap1(y - sy(k), ny);
         const int64_t src = (int64_t)ys * d.pitch + xs;
         const bool b = mask[src] & pullbit;
-        out[2 * Q + k] = load_pop(fin, mom, d, half, 2 * Q + (b ? sopp(k) : k), b ? own : src);
+        out[2 * Q + k] = load_pop(fin, d, half, 2 * Q + (b ? sopp(k) : k), b ? own : src);
     }
 }
 
-// Writes the stored form of node (x, y) from its 22 post-collision values.
-__device__ __forceinline__ void store_node(void *fout, __half *mout,
-                                           const LatDesc &d, bool half,
-                                           int64_t own, const float v[NPOP]) {
+// Writes the stored form of node (x, y) from its 22 post-collision values
+// (FP16 storage: scaled by 1 / w_i and 4 -- correctly rounded quotients --
+// and encoded).
+__device__ __forceinline__ void store_node(void *fout, const LatDesc &d,
+                                           bool half, int64_t own,
+                                           const float v[NPOP]) {
     const int pl = (int)d.plane;
-    if (!half)
+    if (!half) {
         store22_f32(static_cast<float *>(fout) + d.pop_off + own, pl, v, v + Q,
                     v + 2 * Q);
-    else
-        store22_f16(static_cast<__half *>(fout) + d.pop_off + own,
-                    mout + d.mom_off + own, rest_planes(mout, d) + own, pl, pl,
-                    v, v + Q, v + 2 * Q);
+        return;
+    }
+    float fa[Q], fb[Q], gh[QS];
+    for (int i = 0; i < Q; ++i) {
+        fa[i] = __fdiv_rn(v[i], wq(i));
+        fb[i] = __fdiv_rn(v[Q + i], wq(i));
+    }
+    for (int k = 0; k < QS; ++k) gh[k] = 4.0f * v[2 * Q + k];
+    uint32_t wv[NW16];
+    enc_node16(fa, fb, gh, wv);
+    store_words16(static_cast<uint32_t *>(fout) + d.pop_off + own, pl, wv);
 }
 
 // Mask bytes of lattice l over its ghost band (columns -2 .. nx + 1, rows
@@ -143,7 +157,7 @@ __global__ void k_rest_state(const LatDesc *desc, int l, const float *rho_a,
 // The mask must hold no pending flip (force bit == streaming bit).
 __global__ void k_unstream(const LatDesc *desc, int l, const float *canon,
                            const uint8_t *mask_all, uint8_t forcebit,
-                           void *fout, __half *mout, bool half) {
+                           void *fout, bool half) {
     const LatDesc d = desc[l];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -167,16 +181,16 @@ __global__ void k_unstream(const LatDesc *desc, int l, const float *canon,
         const int64_t src = b ? (int64_t)y * d.nx + x : (int64_t)yd * d.nx + xd;
         v[2 * Q + k] = canon[(2 * Q + (b ? sopp(k) : k)) * P + src];
     }
-    store_node(fout, mout, d, half, own, v);
+    store_node(fout, d, half, own, v);
     for_ghosts(x, y, d.nx, d.ny, d.pitch, (int)own,
-               [&](int off) { store_node(fout, mout, d, half, off, v); });
+               [&](int off) { store_node(fout, d, half, off, v); });
 }
 
 // Post-streaming fields of lattice l at step t into canon ([22][ny][nx]);
 // dens ([3][ny][nx]: rho_A, rho_B, C) and dep ([ny][nx]) when not NULL.
 // Nodes solid in s_t (including those turned solid last step) read zero.
 __global__ void k_export(const LatDesc *desc, int l, const void *fin,
-                         const __half *min_, const uint8_t *mask_all,
+                         const uint8_t *mask_all,
                          const double *m_all, long long t, bool half,
                          float *canon, float *dens, double *dep) {
     const LatDesc d = desc[l];
@@ -193,7 +207,7 @@ __global__ void k_export(const LatDesc *desc, int l, const void *fin,
     if (solid) {
         for (int q = 0; q < NPOP; ++q) v[q] = 0.f;
     } else {
-        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        pull_node(fin, mask, d, half, mb.pull, x, y, v);
     }
     if (canon)
         for (int q = 0; q < NPOP; ++q) canon[q * P + n] = v[q];
@@ -211,7 +225,7 @@ __global__ void k_export(const LatDesc *desc, int l, const void *fin,
 // the three mask bits agree (used before replacing fields, so that the
 // stored state has no pending flip).
 __global__ void k_settle(const LatDesc *desc, int l, const void *fin,
-                         const __half *min_, uint8_t *mask_all, double *m_all,
+                         uint8_t *mask_all, double *m_all,
                          LatState *st, long long t, bool half) {
     const LatDesc d = desc[l];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,7 +237,7 @@ __global__ void k_settle(const LatDesc *desc, int l, const void *fin,
     const uint8_t s = mask[own];
     if ((s & mb.force) && !(s & mb.pull)) {
         float v[NPOP];
-        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        pull_node(fin, mask, d, half, mb.pull, x, y, v);
         double ra = 0, rb = 0;
         for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
         const double c = (double)v[18] + v[19] + v[20] + v[21];
@@ -271,7 +285,7 @@ struct ObsPart {
 
 // Sum of the 22 stored values of a node (A, B, solute), as readers decode
 // them.
-__device__ __forceinline__ void stored_sums(const void *fin, const __half *mom,
+__device__ __forceinline__ void stored_sums(const void *fin,
                                             const LatDesc &d, bool half,
                                             int64_t own, float &sa, float &sb,
                                             float &sc) {
@@ -279,16 +293,16 @@ __device__ __forceinline__ void stored_sums(const void *fin, const __half *mom,
     sb = 0.f;
     sc = 0.f;
     for (int i = 0; i < Q; ++i) {
-        sa += load_pop(fin, mom, d, half, i, own);
-        sb += load_pop(fin, mom, d, half, Q + i, own);
+        sa += load_pop(fin, d, half, i, own);
+        sb += load_pop(fin, d, half, Q + i, own);
     }
-    for (int k = 0; k < QS; ++k) sc += load_pop(fin, mom, d, half, 2 * Q + k, own);
+    for (int k = 0; k < QS; ++k) sc += load_pop(fin, d, half, 2 * Q + k, own);
 }
 
 __global__ void __launch_bounds__(32 * OBS_ROWS)
     k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
                   const int64_t *col_base, int ncols_total, const void *fin,
-                  const __half *min_, const uint8_t *mask_all,
+                  const uint8_t *mask_all,
                   const double *m_all, long long t, bool half, ColObs *out) {
     __shared__ ObsPart part[OBS_ROWS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
@@ -309,7 +323,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
             const bool fluid_before = !(sv & mb.pull);
             if (fluid_before) {
                 float sa, sb, sc;
-                stored_sums(fin, min_, d, half, own, sa, sb, sc);
+                stored_sums(fin, d, half, own, sa, sb, sc);
                 if (!(sa + sb < 3.0e38f)) p.nonfin = 1;
                 p.stored[0] += sa;
                 p.stored[1] += sb;
@@ -317,7 +331,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
             }
             if (sv & mb.force) {
                 if (fluid_before) {  // turned solid at the end of the last step
-                    pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+                    pull_node(fin, mask, d, half, mb.pull, x, y, v);
                     double ra = 0, rb = 0;
                     for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
                     p.pend[0] += ra;
@@ -366,7 +380,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
     float v[NPOP];
     // rho_A - rho_B of fluid node (x, y), pulled
     auto phi = [&](int y) {
-        pull_node(fin, min_, mask, d, half, mb.pull, x, y, v);
+        pull_node(fin, mask, d, half, mb.pull, x, y, v);
         float ra = 0.f, rb = 0.f;
         for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
         return ra - rb;

@@ -2,23 +2,22 @@
 // reactive two-component lattice Boltzmann library (sm_103a).
 //
 // Layout in HBM (one handle, `count` lattices packed back to back):
-//   populations: two ping-pong buffers; in each, lattice l owns 22
-//     consecutive planes of (ny + 4) * pitch elements (A: 9, B: 9, solute:
-//     4), rows padded to `pitch` (a multiple of 32 elements, so every row
-//     starts on a 128-byte boundary in FP32 storage);
-//   FP16 storage keeps 20 FP16 planes per lattice (the 8 moving A and 8
-//     moving B populations, then the 4 solute ones, see sp16) and, per
-//     lattice and buffer, a moment block of 5 FP16 reference planes
-//     (w_1 rho~ and w_5 rho~ of A and of B, C~ / 4, see refp) followed by
-//     2 FP32 planes holding the rest populations of A and B (rest_planes);
-//   every plane (populations, moments, mask) has a two-node ghost band
-//     around the lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx,
-//     nx + 1 -- holding the periodic images of the nodes next to the
-//     boundaries; the offsets below point at logical node (0, 0), which
-//     sits at physical row 2 and column 16 of the lattice's planes, so node
-//     (x, y) is at offset y * pitch + x for -2 <= x < nx + 2,
-//     -2 <= y < ny + 2; the nodes next to the boundaries refresh their
-//     images whenever they write;
+//   populations: two ping-pong buffers of 32-bit words; in each, lattice l
+//     owns consecutive planes of (ny + 4) * pitch words, rows padded to
+//     `pitch` (a multiple of 32 words, so every row starts on a 128-byte
+//     boundary):
+//       FP32 storage: 22 planes (A: 9, B: 9, solute: 4);
+//       FP16 storage: 13 planes (see the codec below): 8 planes of half2
+//       deviation pairs {A_i, B_i} of the moving populations, 2 planes of
+//       half2 solute deviation pairs, and 3 FP32 reference planes
+//       (rho~_A, rho~_B, C~);
+//   every plane (populations, mask) has a two-node ghost band around the
+//     lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx, nx + 1 --
+//     holding the periodic images of the nodes next to the boundaries; the
+//     offsets below point at logical node (0, 0), which sits at physical
+//     row 2 and column 16 of the lattice's planes, so node (x, y) is at
+//     offset y * pitch + x for -2 <= x < nx + 2, -2 <= y < ny + 2; the
+//     nodes next to the boundaries refresh their images whenever they write;
 //   mask: one byte per node, read and written in place (see MaskBits);
 //   deposit: one double per node;
 //   per section column: fluid-node counter (closure), initial wall
@@ -34,22 +33,11 @@ namespace lbmk {
 
 constexpr int Q = 9;      // D2Q9 per fluid component
 constexpr int QS = 4;     // D2Q4 solute
-constexpr int NPOP = 22;  // 9 + 9 + 4 planes per lattice
-constexpr int NMOM = 5;   // FP16 storage: reference planes (see refp)
-constexpr int NP16 = 20;  // FP16 storage: population planes (no rest ones)
-constexpr int NREST = 2;  // FP16 storage: FP32 rest planes of A and B
-// FP16 storage: the moment block of a lattice spans 9 half-planes, the 5
-// FP16 references then the 2 FP32 rest planes
-constexpr int MOM_BLOCK = NMOM + 2 * NREST;
-
-// FP16 storage plane of population q (A: 1..8, B: 10..17, solute 18..21;
-// the rest populations 0 and 9 are FP32, in the moment block)
-__host__ __device__ constexpr int sp16(int q) { return q < Q ? q - 1 : q - 2; }
-// FP16 storage reference plane of moving population i (1..8) of component
-// comp: w_1 rho~ and w_5 rho~ of A (planes 0, 1) and of B (2, 3); the
-// solute's C~ / 4 is plane kSolRef
-__host__ __device__ constexpr int refp(int comp, int i) { return 2 * comp + (i >= 5 ? 1 : 0); }
-constexpr int kSolRef = 4;
+constexpr int NPOP = 22;  // FP32 storage: 9 + 9 + 4 planes per lattice
+// FP16 storage: 13 planes of 32-bit words per lattice (see the codec)
+constexpr int NW16 = 13;
+constexpr int W16_SOL = 8;   // half2 {C_0, C_1}, then {C_2, C_3}
+constexpr int W16_REF = 10;  // FP32 rho~_A, rho~_B, C~
 
 // D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
 __host__ __device__ __forceinline__ constexpr int cx(int i) {
@@ -97,8 +85,8 @@ struct alignas(16) LatDesc {
     int32_t nx, ny, pitch, tiles_x;  // pitch >= nx + 2 * XGHOST
     int32_t tile_base, cap_x0, cap_x1, inlet;
     int64_t node_off;   // first node of this lattice in mask / deposit
-    int64_t pop_off;    // first element of plane 0 in a population buffer
-    int64_t mom_off;    // first element of moment plane 0 (FP16 storage)
+    int64_t pop_off;    // first word of plane 0 in a population buffer
+    int64_t pad64_;
     int64_t plane;      // (ny + 4) * pitch: rows -2 .. ny + 1
     int64_t col_off;    // first section column in per-column arrays
     float tau_a, tau_b, inv_tau_a, inv_tau_b, inv_tau_d;
@@ -138,8 +126,6 @@ struct StepArgs {
     const int32_t *tile_lat;
     const void *fin;        // post-collision populations of the last step
     void *fout;             // post-collision populations of this step
-    const __half *min_;     // FP16 storage: moment planes of fin
-    __half *mout;           // FP16 storage: moment planes of fout
     uint8_t *mask;
     double *m;
     int32_t *col_fluid;
@@ -155,70 +141,116 @@ constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
 // ---- FP16 storage codec ------------------------------------------------------
-// A component's moving populations are kept as FP16 deviations from per-node
-// references (FP16, stored once per node, component and weight class), the
-// solute likewise; the rest population is kept in FP32:
-//   moving i = 1..8:  r_c = FP16(w_c rho~) for the class c of i (w_1 or w_5),
-//                     d = 2^10 (f_i - r_c) / w_i,  f_i = r_c + (w_i 2^-10) d
-//   solute k = 0..3:  r = FP16(C / 4),  d = 2^12 (g_k - r),  g_k = r + 2^-12 d
-//   rest:             f_0 in FP32, taking up the moving values' rounding
-// The power-of-two scales are exact; they lift the minority component's
-// small deviations out of FP16's subnormal range (|d| stays far below
-// 65504).  Reading is one fused multiply-add per value, rounded exactly as
-// written here (no contraction into later sums), so all code paths rebuild
-// the same FP32 value from the same bits.
+// FP16 storage keeps, per node, the populations in scaled form -- f^_i =
+// f_i / w_i for the D2Q9 components (the equilibrium is then
+// rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u) with no weight) and g^_k = 4 g_k
+// for the solute -- as FP16 deviations from a per-node FP32 reference:
+//   A, B:   reference rho~ (the rest population f^_0 itself), moving
+//           i = 1..8 as d_i = 2^10 (f^_i - rho~) in FP16, the A and B
+//           deviations of one direction packed in one half2 word;
+//           read back f^_i = rho~ + 2^-10 d_i (one fused multiply-add);
+//   solute: reference C~ (the concentration), d_k = 2^10 (g^_k - C~), two
+//           directions per half2 word; g^_k = C~ + 2^-10 d_k.
+// The deviation carries only the velocity and non-equilibrium parts, so
+// FP16's 11-bit significand applies to a quantity 10-100x smaller than
+// f^_i; the reference is FP32 and local, so the minority component (rho ~
+// 0.006) keeps the majority's relative accuracy.  The power-of-two scale
+// keeps small deviations out of FP16's subnormal range.
+//
+// Mass: the writer quantises every deviation, then adds the exact
+// quantisation error sum_i w_i 2^-10 (d_i - FP16(d_i)) (each term exact in
+// FP32, the sum small) to the stored reference.  Since the reference enters
+// all nine read-backs with weights summing to one, the stored content of
+// the node equals its FP32 post-collision content up to one rounding at the
+// reference's magnitude, and the shift moves no momentum (sum_i w_i e_i =
+// 0).  The solute does the same with weights 1/4.  Readers round every
+// read-back exactly as written here (explicit fused multiply-adds), so
+// all code paths rebuild the same FP32 values from the same bits.
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
-constexpr float kSolScale = 4096.0f;
-constexpr float kInvSolScale = 1.0f / 4096.0f;
 
-// Moving population i (1..8) of a D2Q9 component from its deviation and the
-// reference of its weight class.
-__device__ __forceinline__ float dec_pop(int i, float d, float ref) {
-    return __fmaf_rn(d, wq(i) * kInvDevScale, ref);
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+    return *reinterpret_cast<uint32_t *>(&h);
 }
-// A solute population from its deviation and reference.
-__device__ __forceinline__ float dec_sol(float d, float ref) {
-    return __fmaf_rn(d, kInvSolScale, ref);
+__device__ __forceinline__ __half2 bits_h2(uint32_t w) {
+    return *reinterpret_cast<__half2 *>(&w);
 }
 
-// Encodes the 9 post-collision populations of one component: the moving
-// deviations into dq[1..8], the references of the two weight classes into
-// h1 (w_1 rho~) and h5 (w_5 rho~), the rest population into `rest`.
-// rho~ = f_0 / w_0 (the density times 1 - 3/2 u.u at equilibrium), so every
-// deviation is small.  The rest population takes up the quantisation error
-// of the eight moving ones -- each error f_i - read-back(f_i) is exact in
-// FP32 and tiny, and readers round the read-back exactly as here -- so the
-// stored mass is the FP32 mass up to one rounding at f_0's magnitude.
-// (Solving the rest population from an FP32 sum of all nine values instead
-// biased the mass of long runs by about 1e-8 per step: populations near
-// w_i rho share their low-order bits, so the roundings of such sums are not
-// unbiased.)
-__device__ __forceinline__ void enc9(const float f[Q], __half dq[Q],
-                                     __half &h1, __half &h5, float &rest) {
-    const float rt = f[0] * (1.0f / wq(0));
-    h1 = __float2half_rn(wq(1) * rt);
-    h5 = __float2half_rn(wq(5) * rt);
-    const float ref1 = __half2float(h1), ref5 = __half2float(h5);
-    const float n1 = -ref1 * (kDevScale / wq(1)), n5 = -ref5 * (kDevScale / wq(5));
-    float err = 0.f;
+// Read-back of one scaled value from its FP16 deviation and reference.
+__device__ __forceinline__ float dec16(float d, float ref) {
+    return __fmaf_rn(d, kInvDevScale, ref);
+}
+// The A and B values of one direction from their packed deviations.
+__device__ __forceinline__ void dec_pair(uint32_t w, float ra, float rb,
+                                         float &fa, float &fb) {
+    const float2 d = __half22float2(bits_h2(w));
+    fa = dec16(d.x, ra);
+    fb = dec16(d.y, rb);
+}
+// Solute direction k from the word of its pair (k even: low half).
+__device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
+    const __half2 h = bits_h2(w);
+    return dec16(__half2float((k & 1) ? __high2half(h) : __low2half(h)), ref);
+}
+
+// Encodes the scaled post-collision values of A and B (fa, fb: 9 each)
+// into the 8 direction words w[0..7] and the two references (mass-exact,
+// see above).
+__device__ __forceinline__ void enc_ab(const float fa[Q], const float fb[Q],
+                                       uint32_t w[8], float &ra, float &rb) {
+    const float na = -kDevScale * fa[0], nb = -kDevScale * fb[0];
+    float ea = 0.f, eb = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const float ref = i < 5 ? ref1 : ref5;
-        dq[i] = __float2half_rn(__fmaf_rn(f[i], kDevScale / wq(i), i < 5 ? n1 : n5));
-        err += f[i] - dec_pop(i, __half2float(dq[i]), ref);
+        const float da = __fmaf_rn(fa[i], kDevScale, na);
+        const float db = __fmaf_rn(fb[i], kDevScale, nb);
+        const __half2 h = __floats2half2_rn(da, db);
+        const float2 back = __half22float2(h);
+        ea = __fmaf_rn(wq(i), __fsub_rn(da, back.x), ea);
+        eb = __fmaf_rn(wq(i), __fsub_rn(db, back.y), eb);
+        w[i - 1] = h2_bits(h);
     }
-    rest = f[0] + err;
+    ra = __fmaf_rn(ea, kInvDevScale, fa[0]);
+    rb = __fmaf_rn(eb, kInvDevScale, fb[0]);
 }
 
-// Encodes the 4 solute populations; returns the reference C~ / 4.
-__device__ __forceinline__ __half enc4(const float g[QS], __half dq[QS]) {
-    const float c = (g[0] + g[2]) + (g[1] + g[3]);
-    const __half ch = __float2half_rn(0.25f * c);
-    const float ct = __half2float(ch);
+// Encodes the 4 scaled solute values into two words and the reference.
+__device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
+                                        uint32_t &w23, float &rc) {
+    const float c = 0.25f * __fadd_rn(__fadd_rn(gh[0], gh[2]),
+                                      __fadd_rn(gh[1], gh[3]));
+    const float n = -kDevScale * c;
+    float d[QS];
 #pragma unroll
-    for (int k = 0; k < QS; ++k) dq[k] = __float2half_rn((g[k] - ct) * kSolScale);
-    return ch;
+    for (int k = 0; k < QS; ++k) d[k] = __fmaf_rn(gh[k], kDevScale, n);
+    const __half2 h01 = __floats2half2_rn(d[0], d[1]);
+    const __half2 h23 = __floats2half2_rn(d[2], d[3]);
+    const float2 b01 = __half22float2(h01), b23 = __half22float2(h23);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(d[0], b01.x), __fsub_rn(d[1], b01.y)),
+                              __fadd_rn(__fsub_rn(d[2], b23.x), __fsub_rn(d[3], b23.y)));
+    w01 = h2_bits(h01);
+    w23 = h2_bits(h23);
+    rc = __fmaf_rn(e, 0.25f * kInvDevScale, c);
+}
+
+// The 13 stored words of a node from its scaled post-collision values, in
+// plane order (8 direction pairs, 2 solute pairs, rho~_A, rho~_B, C~).
+__device__ __forceinline__ void enc_node16(const float fa[Q], const float fb[Q],
+                                           const float gh[QS], uint32_t v[NW16]) {
+    float ra, rb, rc;
+    enc_ab(fa, fb, v, ra, rb);
+    enc_sol(gh, v[W16_SOL], v[W16_SOL + 1], rc);
+    v[W16_REF] = __float_as_uint(ra);
+    v[W16_REF + 1] = __float_as_uint(rb);
+    v[W16_REF + 2] = __float_as_uint(rc);
+}
+
+// Density of a D2Q9 component from its scaled populations (the same
+// rounding everywhere it is formed: own nodes, ring cells, both kernels).
+__device__ __forceinline__ float dens_hat(const float f[Q]) {
+    const float s1 = __fadd_rn(__fadd_rn(f[1], f[3]), __fadd_rn(f[2], f[4]));
+    const float s5 = __fadd_rn(__fadd_rn(f[5], f[7]), __fadd_rn(f[6], f[8]));
+    return __fmaf_rn(wq(0), f[0], __fmaf_rn(wq(1), s1, __fmul_rn(wq(5), s5)));
 }
 
 // Reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32, within
@@ -235,19 +267,6 @@ __device__ __forceinline__ float rcp_nr(float x) {
 }
 
 constexpr int XGHOST = 16;  // physical columns before logical column 0
-
-// FP16 storage: the FP32 rest planes of lattice d (A, then B, `plane`
-// apart), at its logical node (0, 0), inside the moment block that starts
-// 5 planes before them.  Both the block start (a multiple of 9 planes of
-// halves) and the 5 reference planes keep them 16-byte aligned.
-__device__ __forceinline__ float *rest_planes(__half *mom, const LatDesc &d) {
-    const int64_t g = (int64_t)GHOST * d.pitch + XGHOST;
-    return reinterpret_cast<float *>(mom + (d.mom_off - g) + NMOM * d.plane) + g;
-}
-__device__ __forceinline__ const float *rest_planes(const __half *mom,
-                                                    const LatDesc &d) {
-    return rest_planes(const_cast<__half *>(mom), d);
-}
 
 // Calls f(offset) for every periodic image of node (x, y) that lies in the
 // ghost band (columns -2 .. nx + 1, rows -2 .. ny + 1, the node itself

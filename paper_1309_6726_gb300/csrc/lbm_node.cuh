@@ -13,26 +13,23 @@ namespace lbmk {
 // ---------------------------------------------------------------------------
 // Population storage policies.
 //
-// Store32: plain FP32 planes.
+// Store32: plain FP32 planes, collision in the populations themselves.
 //
-// Store16: FP16 deviations from per-node FP16 references, one per component
-// and weight class (enc9 / enc4 and dec_pop / dec_sol in lbm_device.cuh).
-// The deviation is small next to rho (it carries velocity and
-// non-equilibrium parts only), so FP16's relative precision applies to a
-// quantity ~10-100x smaller than f_i itself; the minority component
-// (rho ~ 0.006) keeps the same relative accuracy as the majority because the
-// references are local.  The FP32 rest population absorbs the rounding of
-// the eight moving ones so that each node's stored mass equals its FP32
-// mass up to one rounding.
+// Store16: FP16 deviations from per-node FP32 references, A and B of one
+// direction packed in one half2 word (enc_node16 / dec_pair in
+// lbm_device.cuh); the collision works on the scaled populations f_i / w_i
+// and 4 g_k (fluid_update16).
 // ---------------------------------------------------------------------------
 
 struct Store32 {
     static constexpr bool kHalf = false;
     using T = float;
+    static constexpr int kPlanes = NPOP;
 };
 struct Store16 {
     static constexpr bool kHalf = true;
-    using T = __half;
+    using T = uint32_t;
+    static constexpr int kPlanes = NW16;
 };
 
 // D2Q9 BGK relaxation towards the equilibrium of (rho, ux, uy),
@@ -97,85 +94,46 @@ __device__ __forceinline__ void store22_f32(float *__restrict__ p, int plane,
     for (int k = 0; k < QS; ++k) p[(2 * Q + k) * plane] = g[k];
 }
 
-// FP16 storage: the 20 FP16 deviations of a node at p[sp16(q) * plane],
-// its 5 references at mp[refp(c, i) * plane] and mp[kSolRef * plane] and
-// its 2 FP32 rest populations at rp[c * rplane].
-__device__ __forceinline__ void store22_f16(__half *__restrict__ p,
-                                            __half *__restrict__ mp,
-                                            float *__restrict__ rp, int plane,
-                                            int rplane, const float fA[Q],
-                                            const float fB[Q],
-                                            const float g[QS]) {
-    __half dq[Q];
-    float rest;
-    __half h1, h5;
-    enc9(fA, dq, h1, h5, rest);
-    mp[refp(0, 1) * plane] = h1;
-    mp[refp(0, 5) * plane] = h5;
-    rp[0] = rest;
+// FP16 storage: the 13 words of a node at p[w * plane].
+__device__ __forceinline__ void store_words16(uint32_t *__restrict__ p,
+                                              int plane,
+                                              const uint32_t v[NW16]) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) p[sp16(i) * plane] = dq[i];
-    enc9(fB, dq, h1, h5, rest);
-    mp[refp(1, 1) * plane] = h1;
-    mp[refp(1, 5) * plane] = h5;
-    rp[rplane] = rest;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) p[sp16(Q + i) * plane] = dq[i];
-    mp[kSolRef * plane] = enc4(g, dq);
-#pragma unroll
-    for (int k = 0; k < QS; ++k) p[sp16(2 * Q + k) * plane] = dq[k];
+    for (int w = 0; w < NW16; ++w) p[w * plane] = v[w];
 }
 
-// Writes the 22 post-collision values of a node at plane offset `off`.
-template <class S>
+// FP32 storage: writes the 22 post-collision values of a node at plane
+// offset `off`.
 __device__ __forceinline__ void store_node22(const StepArgs &a,
                                              const LatDesc &d, int off,
                                              const float fA[Q],
                                              const float fB[Q],
                                              const float g[QS]) {
-    const int pl = (int)d.plane;
-    if constexpr (!S::kHalf) {
-        store22_f32(static_cast<float *>(a.fout) + d.pop_off + off, pl, fA, fB, g);
-    } else {
-        store22_f16(static_cast<__half *>(a.fout) + d.pop_off + off,
-                    a.mout + d.mom_off + off, rest_planes(a.mout, d) + off, pl,
-                    pl, fA, fB, g);
-    }
+    store22_f32(static_cast<float *>(a.fout) + d.pop_off + off, (int)d.plane,
+                fA, fB, g);
 }
 
-// Writes the 22 post-collision values of the tile node at `o` (planes NT
-// apart) -- a shared-memory tile that bulk tensor stores then copy out:
-// FP32 [22][NT]; FP16 [20][NT] deviations, om [5][NT] references, orest
-// [2][NT] rest populations.
-template <class S, int NT>
-__device__ __forceinline__ void store_tile22(typename S::T *o, __half *om,
-                                             float *orest, const float fA[Q],
-                                             const float fB[Q],
-                                             const float g[QS]) {
-    if constexpr (!S::kHalf)
-        store22_f32(o, NT, fA, fB, g);
-    else
-        store22_f16(o, om, orest, NT, NT, fA, fB, g);
-}
-
-// Everything after the pull, for a node that is fluid in s_t.
-//   fA, fB, g: post-streaming populations of the node (g pulled already);
-//   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
-//   snb: bit i set if x + e_i is solid in s_t;  ns: solid D2Q4 links.
-// put(fA, fB, g) writes the node's own post-collision values; its periodic
-// images in the ghost band are written here.
-// Returns true if the node reached the threshold in this step.
-template <class S, class Put>
-__device__ __forceinline__ bool fluid_update(
-    const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
-    int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
-    const float rhoB_nb[Q], unsigned snb, int ns, Put put) {
-    using T = typename S::T;
-    // ---- moments ----------------------------------------------------------
-    float rA, jAx, jAy, rB, jBx, jBy;
-    moments9(fA, rA, jAx, jAy);
-    moments9(fB, rB, jBx, jBy);
-    // ---- Martys-Chen forces ----------------------------------------------
+// Martys-Chen cohesion and adhesion forces and the Shan-Chen velocity
+// shift of a fluid node (readings c1, c3, c4):
+//   F_s = rho_s (G_ads,s sum_i w_i s(x + e_i) e_i
+//                - G_c sum_i w_i rho_s'(x + e_i) e_i + body force),
+//   u' = sum_s (j_s / tau_s) / sum_s (rho_s / tau_s),
+//   u_s^eq = u' + tau_s F_s / rho_s   (= u' where rho_s < 1e-12).
+// The densities and momenta may be in any units whose density is the
+// component's mass (the FP16 path passes sums of scaled populations with
+// their weights applied).
+struct Shift {
+    float FAx, FAy, FBx, FBy;  // forces on A and B
+    float upx, upy;            // common velocity u'
+    float sA, sB;              // tau_s / rho_s
+};
+__device__ __forceinline__ Shift forces_shift(const LatDesc &d, float rA,
+                                              float rB, float jAx, float jAy,
+                                              float jBx, float jBy,
+                                              const float rhoA_nb[Q],
+                                              const float rhoB_nb[Q],
+                                              unsigned snb) {
+    Shift r;
     float cAx, cAy, cBx, cBy, adx, ady;
     stencil9(rhoB_nb, cAx, cAy);  // A feels B
     stencil9(rhoA_nb, cBx, cBy);  // B feels A
@@ -189,17 +147,39 @@ __device__ __forceinline__ bool fluid_update(
         stencil9(sv, adx, ady);
     }
     // G_ads,A = -g_ads, G_ads,B = +g_ads
-    const float FAx = rA * (d.g_ads * adx - d.g_coh * cAx + d.body_x);
-    const float FAy = rA * (d.g_ads * ady - d.g_coh * cAy);
-    const float FBx = rB * (-d.g_ads * adx - d.g_coh * cBx + d.body_x);
-    const float FBy = rB * (-d.g_ads * ady - d.g_coh * cBy);
-    // ---- Shan-Chen shift and BGK -----------------------------------------
+    r.FAx = rA * (d.g_ads * adx - d.g_coh * cAx + d.body_x);
+    r.FAy = rA * (d.g_ads * ady - d.g_coh * cAy);
+    r.FBx = rB * (-d.g_ads * adx - d.g_coh * cBx + d.body_x);
+    r.FBy = rB * (-d.g_ads * ady - d.g_coh * cBy);
     const float den = rA * d.inv_tau_a + rB * d.inv_tau_b;
     const float iden = den > 1e-30f ? rcp_nr(den) : 0.f;
-    const float upx = (jAx * d.inv_tau_a + jBx * d.inv_tau_b) * iden;
-    const float upy = (jAy * d.inv_tau_a + jBy * d.inv_tau_b) * iden;
-    const float sA = rA > 1e-12f ? d.tau_a * rcp_nr(rA) : 0.f;
-    const float sB = rB > 1e-12f ? d.tau_b * rcp_nr(rB) : 0.f;
+    r.upx = (jAx * d.inv_tau_a + jBx * d.inv_tau_b) * iden;
+    r.upy = (jAy * d.inv_tau_a + jBy * d.inv_tau_b) * iden;
+    r.sA = rA > 1e-12f ? d.tau_a * rcp_nr(rA) : 0.f;
+    r.sB = rB > 1e-12f ? d.tau_b * rcp_nr(rB) : 0.f;
+    return r;
+}
+
+// Everything after the pull, for a node that is fluid in s_t.
+//   fA, fB, g: post-streaming populations of the node (g pulled already);
+//   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
+//   snb: bit i set if x + e_i is solid in s_t;  ns: solid D2Q4 links.
+// put(fA, fB, g) writes the node's own post-collision values; its periodic
+// images in the ghost band are written here.
+// Returns true if the node reached the threshold in this step.
+template <class Put>
+__device__ __forceinline__ bool fluid_update(
+    const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
+    int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
+    const float rhoB_nb[Q], unsigned snb, int ns, Put put) {
+    // ---- moments ----------------------------------------------------------
+    float rA, jAx, jAy, rB, jBx, jBy;
+    moments9(fA, rA, jAx, jAy);
+    moments9(fB, rB, jBx, jBy);
+    const Shift sh = forces_shift(d, rA, rB, jAx, jAy, jBx, jBy, rhoA_nb,
+                                  rhoB_nb, snb);
+    const float FAx = sh.FAx, FAy = sh.FAy, FBx = sh.FBx, FBy = sh.FBy;
+    const float upx = sh.upx, upy = sh.upy, sA = sh.sA, sB = sh.sB;
     bgk9(fA, rA, upx + sA * FAx, upy + sA * FAy, d.inv_tau_a);
     bgk9(fB, rB, upx + sB * FBx, upy + sB * FBy, d.inv_tau_b);
     // ---- solute ----------------------------------------------------------
@@ -242,8 +222,149 @@ __device__ __forceinline__ bool fluid_update(
     put(fA, fB, g);
     // periodic images in the ghost band
     for_ghosts(gx, gy, d.nx, d.ny, d.pitch, own,
-               [&](int off) { store_node22<S>(a, d, off, fA, fB, g); });
+               [&](int off) { store_node22(a, d, off, fA, fB, g); });
     return flagged;
+}
+
+// ---------------------------------------------------------------------------
+// FP16 storage: the same update on scaled populations f^_i = f_i / w_i and
+// g^_k = 4 g_k.
+// ---------------------------------------------------------------------------
+
+// Momentum of a D2Q9 component from its scaled populations,
+// j = sum_i w_i f^_i e_i.
+__device__ __forceinline__ void mom_hat(const float f[Q], float &jx,
+                                        float &jy) {
+    const float d57 = __fsub_rn(f[5], f[7]);
+    jx = __fmaf_rn(wq(1), __fsub_rn(f[1], f[3]),
+                   __fmul_rn(wq(5), __fadd_rn(d57, __fsub_rn(f[8], f[6]))));
+    jy = __fmaf_rn(wq(1), __fsub_rn(f[2], f[4]),
+                   __fmul_rn(wq(5), __fadd_rn(d57, __fsub_rn(f[6], f[8]))));
+}
+
+// BGK relaxation of scaled populations towards
+//   f^eq_i = rho (1 + 3 e_i.u + 9/2 (e_i.u)^2 - 3/2 u.u),
+// pairwise as bgk9.  The rest value closes the mass exactly as dens_hat
+// forms it: w_0 f^eq_0 = rho - (w_1 S_1 + w_5 S_5), the quotient by the
+// FP32 w_0 taken as a product with 9/4 and one fused multiply-add
+// correction (9/4 alone would make w_0 f^eq_0 exceed its target by 7e-9,
+// mass created at every collision).
+__device__ __forceinline__ void bgk9_hat(float f[Q], float rho, float ux,
+                                         float uy, float omega) {
+    const float a = rho * (1.0f - 1.5f * (ux * ux + uy * uy));
+    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+    const float up = ux + uy, um = ux - uy;
+    const float sx_ = a + r45 * ux * ux, sy_ = a + r45 * uy * uy;
+    const float sp = a + r45 * up * up, sm = a + r45 * um * um;
+    const float px = r3 * ux, py = r3 * uy, pp = r3 * up, pm = r3 * um;
+    float feq[Q];
+    feq[1] = sx_ + px;
+    feq[3] = sx_ - px;
+    feq[2] = sy_ + py;
+    feq[4] = sy_ - py;
+    feq[5] = sp + pp;   // (1, 1)
+    feq[7] = sp - pp;   // (-1, -1)
+    feq[8] = sm + pm;   // (1, -1)
+    feq[6] = sm - pm;   // (-1, 1)
+    const float s1 = __fadd_rn(__fadd_rn(feq[1], feq[3]), __fadd_rn(feq[2], feq[4]));
+    const float s5 = __fadd_rn(__fadd_rn(feq[5], feq[7]), __fadd_rn(feq[6], feq[8]));
+    const float v = __fsub_rn(rho, __fmaf_rn(wq(1), s1, __fmul_rn(wq(5), s5)));
+    const float y0 = __fmul_rn(v, 2.25f);
+    feq[0] = __fmaf_rn(__fmaf_rn(-wq(0), y0, v), 2.25f, y0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = f[i] + omega * (feq[i] - f[i]);
+}
+
+// Everything after the pull for a node fluid in s_t, FP16 storage.
+//   fA, fB, g: scaled post-streaming populations of the node;
+//   rA, rB: its densities (dens_hat of fA, fB, as in the density frame);
+//   nb: densities {rho_A, rho_B} at x + e_i (index 1..8; 0 if solid);
+//   snb, ns: as for fluid_update.
+// put(words) writes the node's 13 stored words; its periodic images in the
+// ghost band are written here.  Returns true if the node reached the
+// threshold in this step.
+template <class Put>
+__device__ __forceinline__ bool fluid_update16(
+    const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
+    int own, float fA[Q], float fB[Q], float g[QS], float rA, float rB,
+    const float2 nb[Q], unsigned snb, int ns, Put put) {
+    float jAx, jAy, jBx, jBy;
+    mom_hat(fA, jAx, jAy);
+    mom_hat(fB, jBx, jBy);
+    float nA[Q], nB[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        nA[i] = nb[i].x;
+        nB[i] = nb[i].y;
+    }
+    const Shift sh = forces_shift(d, rA, rB, jAx, jAy, jBx, jBy, nA, nB, snb);
+    bgk9_hat(fA, rA, sh.upx + sh.sA * sh.FAx, sh.upy + sh.sA * sh.FAy, d.inv_tau_a);
+    bgk9_hat(fB, rB, sh.upx + sh.sB * sh.FBx, sh.upy + sh.sB * sh.FBy, d.inv_tau_b);
+    // ---- solute (scaled: g^eq_k = C (1 + 2 e_k.u), C = sum_k g^_k / 4) --
+    const float rt = rA + rB;
+    const float irt = rt > 1e-30f ? rcp_nr(rt) : 0.f;
+    const float ux = ((jAx + jBx) + 0.5f * (sh.FAx + sh.FBx)) * irt;
+    const float uy = ((jAy + jBy) + 0.5f * (sh.FAy + sh.FBy)) * irt;
+    {
+        const bool inl = d.inlet && gx == 0;
+        const float c = inl ? d.c_in : 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
+        const float hx2 = 2.0f * c * ux, hy2 = 2.0f * c * uy;
+        const float geq[QS] = {c + hx2, c + hy2, c - hx2, c - hy2};
+        const float om = inl ? 1.0f : d.inv_tau_d;
+#pragma unroll
+        for (int k = 0; k < QS; ++k) g[k] = g[k] + om * (geq[k] - g[k]);
+    }
+    // ---- surface reaction, deposit, threshold ----------------------------
+    bool flagged = false;
+    if (ns > 0 && rA > rB) {
+        const float cs = 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
+        const float lost = fminf(1.0f, d.k_r * (float)ns);
+#pragma unroll
+        for (int k = 0; k < QS; ++k) g[k] -= g[k] * lost;
+        const double dM = (double)cs * (double)lost;
+        double *mp = a.m + d.node_off + own;
+        const double mv = *mp + dM;
+        *mp = mv;
+        if (mv >= d.m_th) {
+            flagged = true;
+            if (gx >= d.cap_x0 && gx < d.cap_x1) {
+                const int old = atomicSub(&a.col_fluid[d.col_off + gx - d.cap_x0], 1);
+                if (old == 1) atomicMin(&a.st[l].closure, (unsigned long long)(t + 1));
+            }
+        }
+    }
+    if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
+    uint32_t v[NW16];
+    enc_node16(fA, fB, g, v);
+    put(v);
+    // periodic images in the ghost band
+    uint32_t *out = static_cast<uint32_t *>(a.fout) + d.pop_off;
+    for_ghosts(gx, gy, d.nx, d.ny, d.pitch, own,
+               [&](int off) { store_words16(out + off, (int)d.plane, v); });
+    return flagged;
+}
+
+// FP16 storage: a node flagged in the previous step hands its scaled
+// post-streaming content (weights applied) and its deposit to the ledger.
+__device__ __forceinline__ void retire_node16(const StepArgs &a,
+                                              const LatDesc &d, int l,
+                                              int own, const float fA[Q],
+                                              const float fB[Q],
+                                              const float g[QS]) {
+    double ra = 0, rb = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        ra += (double)wq(i) * fA[i];
+        rb += (double)wq(i) * fB[i];
+    }
+    const double c = 0.25 * ((double)g[0] + g[1] + g[2] + g[3]);
+    double *mp = a.m + d.node_off + own;
+    const double mv = *mp;
+    *mp = 0.0;
+    atomicAdd(&a.st[l].ledger[0], ra);
+    atomicAdd(&a.st[l].ledger[1], rb);
+    atomicAdd(&a.st[l].ledger[2], c);
+    atomicAdd(&a.st[l].ledger[3], mv);
 }
 
 // A node flagged in the previous step: its post-streaming fluid, solute and

@@ -22,7 +22,8 @@
 //
 // Floating point: FP32 arithmetic in the order of the collision formulas;
 // the deposit and its threshold test are FP64.  Populations are stored as
-// FP32 (Store32) or as FP16 deviations (Store16, see below).
+// FP32 (Store32) or as FP16 deviations from FP32 references (Store16, see
+// lbm_device.cuh).
 #include "lbm_node.cuh"
 
 namespace lbmk {
@@ -47,10 +48,9 @@ __device__ __forceinline__ unsigned pull_bits(const uint8_t (*sm)[HX], int hy,
     return bb;
 }
 
-// Pulls the 9 populations of component `comp` into node (gx, gy).
-template <class S>
-__device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
-                                      const __half *__restrict__ mom,
+// Pulls the 9 populations of component `comp` into node (gx, gy), FP32
+// storage.
+__device__ __forceinline__ void pull9(const float *__restrict__ fin,
                                       const LatDesc &d, int comp, int gx,
                                       int gxm, int gxp, int gy, int gym,
                                       int gyp, unsigned bb, float f[Q]) {
@@ -62,25 +62,13 @@ __device__ __forceinline__ void pull9(const typename S::T *__restrict__ fin,
         const bool b = (bb >> i) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
         const int qi = b ? opp(i) : i;
-        const int q = comp * Q + qi;
-        if constexpr (!S::kHalf) {
-            f[i] = __ldg(fin + d.pop_off + q * d.plane + src);
-        } else if (i == 0) {
-            f[0] = rest_planes(mom, d)[comp * d.plane + own];
-        } else {
-            const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
-            // opposite directions share a weight class: i's reference
-            const float rt = __half2float(mom[d.mom_off + refp(comp, i) * d.plane + src]);
-            f[i] = dec_pop(i, dv, rt);
-        }
+        f[i] = __ldg(fin + d.pop_off + (comp * Q + qi) * d.plane + src);
     }
 }
 
-// Pulls the 4 solute populations into node (gx, gy); bounce-back where the
-// D2Q4 source was solid.
-template <class S>
-__device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
-                                      const __half *__restrict__ mom,
+// Pulls the 4 solute populations into node (gx, gy), FP32 storage;
+// bounce-back where the D2Q4 source was solid.
+__device__ __forceinline__ void pull4(const float *__restrict__ fin,
                                       const LatDesc &d, int gx, int gxm,
                                       int gxp, int gy, int gym, int gyp,
                                       unsigned bb4, float g[QS]) {
@@ -91,22 +79,96 @@ __device__ __forceinline__ void pull4(const typename S::T *__restrict__ fin,
         const int syy = sy(k) > 0 ? gym : (sy(k) < 0 ? gyp : gy);
         const bool b = (bb4 >> k) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
-        const int q = 2 * Q + (b ? sopp(k) : k);
-        if constexpr (!S::kHalf) {
-            g[k] = __ldg(fin + d.pop_off + q * d.plane + src);
-        } else {
-            const float dv = __half2float(fin[d.pop_off + sp16(q) * d.plane + src]);
-            const float ct = __half2float(mom[d.mom_off + kSolRef * d.plane + src]);
-            g[k] = dec_sol(dv, ct);
-        }
+        g[k] = __ldg(fin + d.pop_off + (2 * Q + (b ? sopp(k) : k)) * d.plane + src);
     }
+}
+
+// FP16 storage: the scaled A and B populations pulled into node (gx, gy)
+// (bb: bounce-back bits of the 9 directions).
+__device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
+                                         const LatDesc &d, int gx, int gxm,
+                                         int gxp, int gy, int gym, int gyp,
+                                         unsigned bb, float fA[Q],
+                                         float fB[Q]) {
+    const uint32_t *w = fin + d.pop_off;
+    const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
+    const int64_t own = (int64_t)gy * d.pitch + gx;
+    fA[0] = __ldg(ref + own);
+    fB[0] = __ldg(ref + d.plane + own);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int sxx = cx(i) > 0 ? gxm : (cx(i) < 0 ? gxp : gx);
+        const int syy = cy(i) > 0 ? gym : (cy(i) < 0 ? gyp : gy);
+        const bool b = (bb >> i) & 1u;
+        const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
+        const int qi = b ? opp(i) : i;
+        dec_pair(__ldg(w + (qi - 1) * d.plane + src), __ldg(ref + src),
+                 __ldg(ref + d.plane + src), fA[i], fB[i]);
+    }
+}
+
+// FP16 storage: the 4 scaled solute populations of node (gx, gy) (bb4:
+// bounce-back bits of the 4 directions).
+__device__ __forceinline__ void pull16s(const uint32_t *__restrict__ fin,
+                                        const LatDesc &d, int gx, int gxm,
+                                        int gxp, int gy, int gym, int gyp,
+                                        unsigned bb4, float g[QS]) {
+    const uint32_t *w = fin + d.pop_off;
+    const float *ref = reinterpret_cast<const float *>(w + (W16_REF + 2) * d.plane);
+    const int64_t own = (int64_t)gy * d.pitch + gx;
+#pragma unroll
+    for (int k = 0; k < QS; ++k) {
+        const int sxx = sx(k) > 0 ? gxm : (sx(k) < 0 ? gxp : gx);
+        const int syy = sy(k) > 0 ? gym : (sy(k) < 0 ? gyp : gy);
+        const bool b = (bb4 >> k) & 1u;
+        const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
+        const int qk = b ? sopp(k) : k;
+        g[k] = dec_sol16(__ldg(w + (W16_SOL + (qk >> 1)) * d.plane + src), qk,
+                         __ldg(ref + src));
+    }
+}
+
+// Both components' populations (scaled for FP16) and their densities, as
+// the TMA kernel forms them.
+template <class S>
+__device__ __forceinline__ void pull_ab(const StepArgs &a, const LatDesc &d,
+                                        int gx, int gxm, int gxp, int gy,
+                                        int gym, int gyp, unsigned bb,
+                                        float fA[Q], float fB[Q], float &ra,
+                                        float &rb) {
+    if constexpr (!S::kHalf) {
+        const float *fin = static_cast<const float *>(a.fin);
+        pull9(fin, d, 0, gx, gxm, gxp, gy, gym, gyp, bb, fA);
+        pull9(fin, d, 1, gx, gxm, gxp, gy, gym, gyp, bb, fB);
+        ra = 0.f;
+        rb = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+    } else {
+        pull16ab(static_cast<const uint32_t *>(a.fin), d, gx, gxm, gxp, gy,
+                 gym, gyp, bb, fA, fB);
+        ra = dens_hat(fA);
+        rb = dens_hat(fB);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void pull_sol(const StepArgs &a, const LatDesc &d,
+                                         int gx, int gxm, int gxp, int gy,
+                                         int gym, int gyp, unsigned bb4,
+                                         float g[QS]) {
+    if constexpr (!S::kHalf)
+        pull4(static_cast<const float *>(a.fin), d, gx, gxm, gxp, gy, gym, gyp,
+              bb4, g);
+    else
+        pull16s(static_cast<const uint32_t *>(a.fin), d, gx, gxm, gxp, gy,
+                gym, gyp, bb4, g);
 }
 
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY)
     k_step(StepArgs a) {
     using TL = Tile<TX, TY>;
-    using T = typename S::T;
     __shared__ uint8_t smask[TL::HY][TL::HX];
     __shared__ float srho[2][TL::RY][TL::RX];
     __shared__ long long s_t;
@@ -114,7 +176,6 @@ __global__ void __launch_bounds__(TX *TY)
     const int tid = threadIdx.x;
     const int l = a.tile_lat[blockIdx.x];
     const LatDesc d = a.desc[l];
-    const T *__restrict__ fin = static_cast<const T *>(a.fin);
     const int nx = d.nx, ny = d.ny;
     const int local = blockIdx.x - d.tile_base;
     const int tx0 = (local % d.tiles_x) * TX;
@@ -141,14 +202,11 @@ __global__ void __launch_bounds__(TX *TY)
     const uint8_t s_own = smask[ly + 2][lx + 2];
     const bool own_pull_fluid = !(s_own & mb.pull);
     float fA[Q], fB[Q];
+    float ra = 0.f, rb = 0.f;
     {
-        float ra = 0.f, rb = 0.f;
         if (own_pull_fluid) {
             const unsigned bb = pull_bits<TL::HX>(smask, ly + 2, lx + 2, mb.pull);
-            pull9<S>(fin, a.min_, d, 0, gx, gxm, gxp, gy, gym, gyp, bb, fA);
-            pull9<S>(fin, a.min_, d, 1, gx, gxm, gxp, gy, gym, gyp, bb, fB);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+            pull_ab<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb, fA, fB, ra, rb);
         }
         const bool force_solid = s_own & mb.force;
         srho[0][ly + 1][lx + 1] = force_solid ? 0.f : ra;
@@ -162,22 +220,17 @@ __global__ void __launch_bounds__(TX *TY)
         else if (r < 2 * TL::RX + TY) { ry = 1 + r - 2 * TL::RX; rx = 0; }
         else { ry = 1 + r - 2 * TL::RX - TY; rx = TL::RX - 1; }
         const uint8_t s = smask[ry + 1][rx + 1];
-        float ra = 0.f, rb = 0.f;
+        float qa = 0.f, qb = 0.f;
         if (!(s & mb.force)) {
             const int X = wrapg(tx0 - 1 + rx, nx), Y = wrapg(ty0 - 1 + ry, ny);
             const int Xm = wrap1(X - 1, nx), Xp = wrap1(X + 1, nx);
             const int Ym = wrap1(Y - 1, ny), Yp = wrap1(Y + 1, ny);
             const unsigned bb = pull_bits<TL::HX>(smask, ry + 1, rx + 1, mb.pull);
-            float f[Q];
-            pull9<S>(fin, a.min_, d, 0, X, Xm, Xp, Y, Ym, Yp, bb, f);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) ra += f[i];
-            pull9<S>(fin, a.min_, d, 1, X, Xm, Xp, Y, Ym, Yp, bb, f);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) rb += f[i];
+            float f[Q], h[Q];
+            pull_ab<S>(a, d, X, Xm, Xp, Y, Ym, Yp, bb, f, h, qa, qb);
         }
-        srho[0][ry][rx] = ra;
-        srho[1][ry][rx] = rb;
+        srho[0][ry][rx] = qa;
+        srho[1][ry][rx] = qb;
     }
     __syncthreads();
 
@@ -195,8 +248,11 @@ __global__ void __launch_bounds__(TX *TY)
             const uint8_t nb = s_own | mb.next;
             if (own_pull_fluid) {
                 float g[QS];
-                pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
-                retire_node(a, d, l, own, fA, fB, g);
+                pull_sol<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
+                if constexpr (S::kHalf)
+                    retire_node16(a, d, l, own, fA, fB, g);
+                else
+                    retire_node(a, d, l, own, fA, fB, g);
             }
             if (nb != s_own) mask_store(mask, own, gx, gy, nx, ny, d.pitch, nb);
         } else {
@@ -208,12 +264,25 @@ __global__ void __launch_bounds__(TX *TY)
                 rBn[i] = srho[1][ly + 1 + cy(i)][lx + 1 + cx(i)];
                 if (smask[hy + cy(i)][hx + cx(i)] & mb.force) snb |= 1u << i;
             }
-            pull4<S>(fin, a.min_, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
-            const bool flagged = fluid_update<S>(
-                a, d, l, t, gx, gy, own, fA, fB, g, rAn, rBn, snb, ns,
-                [&](const float *pa, const float *pb, const float *pg) {
-                    store_node22<S>(a, d, own, pa, pb, pg);
-                });
+            pull_sol<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
+            bool flagged;
+            if constexpr (S::kHalf) {
+                float2 nbv[Q];
+#pragma unroll
+                for (int i = 1; i < Q; ++i) nbv[i] = make_float2(rAn[i], rBn[i]);
+                flagged = fluid_update16(
+                    a, d, l, t, gx, gy, own, fA, fB, g, ra, rb, nbv, snb, ns,
+                    [&](const uint32_t *v) {
+                        store_words16(static_cast<uint32_t *>(a.fout) + d.pop_off + own,
+                                      (int)d.plane, v);
+                    });
+            } else {
+                flagged = fluid_update(
+                    a, d, l, t, gx, gy, own, fA, fB, g, rAn, rBn, snb, ns,
+                    [&](const float *pa, const float *pb, const float *pg) {
+                        store_node22(a, d, own, pa, pb, pg);
+                    });
+            }
             if (flagged) mask_store(mask, own, gx, gy, nx, ny, d.pitch, s_own | mb.next);
         }
     }

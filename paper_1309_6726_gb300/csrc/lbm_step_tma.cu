@@ -5,18 +5,17 @@
 //   * the kernel is persistent: a grid of (SM count x resident blocks)
 //     walks the tiles of every lattice of the batch;
 //   * for each tile of TX x TY nodes, one thread issues a 3-D bulk tensor
-//     copy (cp.async.bulk.tensor) of the population planes over the tile
-//     plus a halo of 2 rows and 4 (FP32) or 8 (FP16) columns -- the x start
-//     stays 16-byte aligned -- into shared memory, completing on an
-//     mbarrier; FP16 storage adds copies of the 5 reference planes and the
-//     2 FP32 rest planes; the mask box and the lattice descriptor come
-//     with them;
+//     copy (cp.async.bulk.tensor) of the population planes (32-bit words:
+//     22 FP32 values, or the 13 words of FP16 storage) over the tile plus
+//     a halo of 2 rows and 4 columns -- the x start stays 16-byte aligned
+//     -- into shared memory, completing on an mbarrier; the mask box and
+//     the lattice descriptor come with it;
 //   * two stages: the copy of the next tile is in flight while the current
 //     one is computed;
 //   * all pulls -- the tile's own nodes and the one-node density ring the
 //     cohesion stencil needs -- then read shared memory at fixed offsets;
 //   * the tile's post-collision values go to a shared output tile that one
-//     bulk tensor store per tile (and plane group) copies out;
+//     bulk tensor store per tile copies out;
 //   * the lattice planes carry a two-node periodic ghost band (rows and
 //     columns), so every copy reads valid neighbours and nothing needs
 //     patching;
@@ -136,31 +135,26 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src,
 
 template <class S, int TX_, int TY_>
 struct TmaTile {
-    using T = typename S::T;
+    using T = typename S::T;  // 32-bit words: FP32 values or FP16 pairs
     static constexpr int TX = TX_, TY = TY_;
     static constexpr int NT = TX * TY;
     static constexpr int NW = NT / 32;            // warps
-    static constexpr int XO = S::kHalf ? 8 : 4;  // halo columns copied
+    static constexpr int XO = 4;                  // halo columns copied (16 B)
     static constexpr int BX = TX + 2 * XO;        // box width
     static constexpr int BY = TY + 4;             // box height (halo 2)
-    static constexpr int PL = BX * BY;            // elements per plane
+    static constexpr int PL = BX * BY;            // words per plane
     static constexpr int MXO = 16;                // mask box: 16-byte aligned
     static constexpr int MBX = TX + 2 * MXO;
-    // population planes in a stage: 22 FP32, or 20 FP16 deviations plus
-    // 5 FP16 references and 2 FP32 rest planes
-    static constexpr int NPL = S::kHalf ? NP16 : NPOP;
-    static constexpr int POP_BYTES = NPL * PL * (int)sizeof(T);
-    static constexpr int MOM_BYTES = S::kHalf ? NMOM * PL * 2 : 0;
-    static constexpr int REST_BYTES = S::kHalf ? NREST * PL * 4 : 0;
-    static constexpr int REST_OFF = POP_BYTES + MOM_BYTES;  // within a stage
+    // population planes of a stage: 22 FP32, or the 13 words of FP16 storage
+    static constexpr int NPL = S::kPlanes;
+    static constexpr int POP_BYTES = NPL * PL * 4;
     static constexpr int MASK_BYTES = (MBX * BY + 127) / 128 * 128;
-    static constexpr int STAGE =
-        ((POP_BYTES + MOM_BYTES + REST_BYTES + 127) / 128 * 128) + MASK_BYTES;
+    static constexpr int STAGE = ((POP_BYTES + 127) / 128 * 128) + MASK_BYTES;
     static constexpr int MASK_OFF = STAGE - MASK_BYTES;  // within a stage
-    static constexpr int TX_BYTES =
-        POP_BYTES + MOM_BYTES + REST_BYTES + MBX * BY + 128;
+    static constexpr int TX_BYTES = POP_BYTES + MBX * BY + 128;
     static constexpr int RX = TX + 2, RY = TY + 2;  // density frame
     static constexpr int NRING = 2 * RX + 2 * TY;
+    // FP32: two planes rho_A, rho_B; FP16: one plane of {rho_A, rho_B}
     static constexpr int RHO_BYTES = 2 * RX * RY * 4;
     static constexpr int RHO_AL = (RHO_BYTES + 127) / 128 * 128;
     // Two stages: the copy of the next tile lands while this one is
@@ -171,23 +165,17 @@ struct TmaTile {
     static constexpr int NSL = NS + 1;
     static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
     static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
-    // The tile's post-collision output, [22][TY][TX] FP32 or [20][TY][TX]
-    // FP16 + [5][TY][TX] FP16 references + [2][TY][TX] FP32 rest planes,
-    // written by bulk tensor stores -- where it fits.
-    static constexpr int OUT_POP = NPL * NT * (int)sizeof(T);
-    static constexpr int OUT_REST = OUT_POP + (S::kHalf ? NMOM * NT * 2 : 0);
-    static constexpr int OUT_BYTES =
-        (OUT_REST + (S::kHalf ? NREST * NT * 4 : 0) + 127) / 128 * 128;
+    // The tile's post-collision output, [NPL][TY][TX] words, written by
+    // bulk tensor stores -- where it fits.
+    static constexpr int OUT_BYTES = (NPL * NT * 4 + 127) / 128 * 128;
     static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
     static constexpr bool TS = OUT_OFF + OUT_BYTES + 128 <= 232448;
     static constexpr int BAR_OFF = OUT_OFF + (TS ? OUT_BYTES : 0);
     static constexpr int SMEM = BAR_OFF + 128;
     static_assert(SMEM <= 232448, "shared memory per block");
-    static_assert((TX * (int)sizeof(T)) % 16 == 0, "store box row");
-    static_assert(POP_BYTES % 16 == 0 && MOM_BYTES % 16 == 0 &&
-                      REST_OFF % 16 == 0 && OUT_REST % 16 == 0,
-                  "stage alignment");
-    static_assert((BX * (int)sizeof(T)) % 16 == 0, "TMA box row");
+    static_assert((TX * 4) % 16 == 0, "store box row");
+    static_assert(POP_BYTES % 16 == 0, "stage alignment");
+    static_assert((BX * 4) % 16 == 0, "TMA box row");
     // ring cells per warp: whole warps take the ring (5 of 8 at 64 x 4),
     // since a warp costs the same issue slots with 10 lanes active as with
     // 32 (spreading it thinly over every warp measured 4 % slower for FP16)
@@ -197,93 +185,127 @@ struct TmaTile {
 };
 
 // The 9 populations of component `comp` pulled into the node at stage cell
-// `c`, from shared memory (bb: bounce-back bits).  BB = false: no source is
-// solid, every address is the node's cell plus a constant.  FP16 storage:
-// deviations and references from the stage, the rest population (which
-// never moves) from the FP32 rest planes `rest`.
-template <class S, class TT, bool BB>
-__device__ __forceinline__ void spull9(const typename S::T *tile,
-                                       const __half *mom, const float *rest,
-                                       int comp, int c, unsigned bb,
-                                       float f[Q]) {
+// `c`, from shared memory (bb: bounce-back bits), FP32 storage.  BB = false:
+// no source is solid, every address is the node's cell plus a constant.
+template <class TT, bool BB>
+__device__ __forceinline__ void spull9(const float *tile, int comp, int c,
+                                       unsigned bb, float f[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool b = BB && ((bb >> i) & 1u);
         const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
         const int qi = b ? opp(i) : i;
-        if constexpr (!S::kHalf) {
-            f[i] = tile[(comp * Q + qi) * TT::PL + cell];
-        } else if (i == 0) {
-            f[0] = rest[comp * TT::PL + c];
-        } else {
-            // opposite directions share a weight class: i's reference
-            f[i] = dec_pop(i, __half2float(tile[sp16(comp * Q + qi) * TT::PL + cell]),
-                           __half2float(mom[refp(comp, i) * TT::PL + cell]));
-        }
+        f[i] = tile[(comp * Q + qi) * TT::PL + cell];
     }
 }
 
-template <class S, class TT, bool BB>
-__device__ __forceinline__ void spull4(const typename S::T *tile,
-                                       const __half *mom, int c, unsigned bb4,
+template <class TT, bool BB>
+__device__ __forceinline__ void spull4(const float *tile, int c, unsigned bb4,
                                        float g[QS]) {
 #pragma unroll
     for (int k = 0; k < QS; ++k) {
         const bool b = BB && ((bb4 >> k) & 1u);
         const int cell = b ? c : c - sy(k) * TT::BX - sx(k);
-        const int q = 2 * Q + (b ? sopp(k) : k);
-        if constexpr (!S::kHalf) {
-            g[k] = tile[q * TT::PL + cell];
+        g[k] = tile[(2 * Q + (b ? sopp(k) : k)) * TT::PL + cell];
+    }
+}
+
+// FP16 storage: the scaled A and B populations pulled into the node at
+// stage cell c -- one packed word and the source's two FP32 references per
+// direction; the rest populations are the node's own references.
+template <class TT, bool BB>
+__device__ __forceinline__ void spull16ab(const uint32_t *tile, int c,
+                                          unsigned bb, float fA[Q],
+                                          float fB[Q]) {
+    const float *ref = reinterpret_cast<const float *>(tile) + W16_REF * TT::PL;
+    fA[0] = ref[c];
+    fB[0] = ref[TT::PL + c];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const bool b = BB && ((bb >> i) & 1u);
+        const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
+        const int qi = b ? opp(i) : i;
+        dec_pair(tile[(qi - 1) * TT::PL + cell], ref[cell], ref[TT::PL + cell],
+                 fA[i], fB[i]);
+    }
+}
+
+// FP16 storage: the 4 scaled solute populations (bb: the D2Q9 bounce-back
+// bits; D2Q4 direction k is D2Q9 direction k + 1).
+template <class TT, bool BB>
+__device__ __forceinline__ void spull16s(const uint32_t *tile, int c,
+                                         unsigned bb, float g[QS]) {
+    const float *ref = reinterpret_cast<const float *>(tile) + (W16_REF + 2) * TT::PL;
+#pragma unroll
+    for (int k = 0; k < QS; ++k) {
+        const bool b = BB && ((bb >> (k + 1)) & 1u);
+        const int cell = b ? c : c - sy(k) * TT::BX - sx(k);
+        const int qk = b ? sopp(k) : k;
+        g[k] = dec_sol16(tile[(W16_SOL + (qk >> 1)) * TT::PL + cell], qk, ref[cell]);
+    }
+}
+
+// The 22 populations of the node at stage cell c (scaled for FP16).
+// `fast` (bb == 0 on every lane that calls) takes the path without
+// bounce-back selects; the other path gives the same values for bb == 0,
+// so a warp with any bounce-back lane runs that one alone.
+template <class S, class TT>
+__device__ __forceinline__ void spull22(const typename S::T *tile, int c,
+                                        unsigned bb, bool fast, float fA[Q],
+                                        float fB[Q], float g[QS]) {
+    if constexpr (!S::kHalf) {
+        if (fast) {
+            spull9<TT, false>(tile, 0, c, 0u, fA);
+            spull9<TT, false>(tile, 1, c, 0u, fB);
+            spull4<TT, false>(tile, c, 0u, g);
         } else {
-            g[k] = dec_sol(__half2float(tile[sp16(q) * TT::PL + cell]),
-                           __half2float(mom[kSolRef * TT::PL + cell]));
+            spull9<TT, true>(tile, 0, c, bb, fA);
+            spull9<TT, true>(tile, 1, c, bb, fB);
+            spull4<TT, true>(tile, c, (bb >> 1) & 0xFu, g);
+        }
+    } else {
+        if (fast) {
+            spull16ab<TT, false>(tile, c, 0u, fA, fB);
+            spull16s<TT, false>(tile, c, 0u, g);
+        } else {
+            spull16ab<TT, true>(tile, c, bb, fA, fB);
+            spull16s<TT, true>(tile, c, bb, g);
         }
     }
 }
 
-// The 22 populations of the node at stage cell c.  `fast` (bb == 0 on
-// every lane that calls) takes the path without bounce-back selects; the
-// other path gives the same values for bb == 0, so a warp with any
-// bounce-back lane runs that one alone.
+// Densities of both components at stage cell c (`fast` as for spull22),
+// formed as the node's own update forms them.
 template <class S, class TT>
-__device__ __forceinline__ void spull22(const typename S::T *tile,
-                                        const __half *mom, const float *rest,
-                                        int c, unsigned bb, bool fast,
-                                        float fA[Q], float fB[Q], float g[QS]) {
-    if (fast) {
-        spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, fA);
-        spull9<S, TT, false>(tile, mom, rest, 1, c, 0u, fB);
-        spull4<S, TT, false>(tile, mom, c, 0u, g);
+__device__ __forceinline__ void sdens(const typename S::T *tile, int c,
+                                      unsigned bb, bool fast, float &ra,
+                                      float &rb) {
+    float f[Q], h[Q];
+    if constexpr (!S::kHalf) {
+        ra = 0.f;
+        rb = 0.f;
+        if (fast) {
+            spull9<TT, false>(tile, 0, c, 0u, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ra += f[i];
+            spull9<TT, false>(tile, 1, c, 0u, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rb += f[i];
+        } else {
+            spull9<TT, true>(tile, 0, c, bb, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ra += f[i];
+            spull9<TT, true>(tile, 1, c, bb, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rb += f[i];
+        }
     } else {
-        spull9<S, TT, true>(tile, mom, rest, 0, c, bb, fA);
-        spull9<S, TT, true>(tile, mom, rest, 1, c, bb, fB);
-        spull4<S, TT, true>(tile, mom, c, (bb >> 1) & 0xFu, g);
-    }
-}
-
-// Densities of both components at stage cell c (`fast` as for spull22).
-template <class S, class TT>
-__device__ __forceinline__ void sdens(const typename S::T *tile,
-                                      const __half *mom, const float *rest,
-                                      int c, unsigned bb, bool fast,
-                                      float &ra, float &rb) {
-    float f[Q];
-    ra = 0.f;
-    rb = 0.f;
-    if (fast) {
-        spull9<S, TT, false>(tile, mom, rest, 0, c, 0u, f);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) ra += f[i];
-        spull9<S, TT, false>(tile, mom, rest, 1, c, 0u, f);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rb += f[i];
-    } else {
-        spull9<S, TT, true>(tile, mom, rest, 0, c, bb, f);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) ra += f[i];
-        spull9<S, TT, true>(tile, mom, rest, 1, c, bb, f);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rb += f[i];
+        if (fast)
+            spull16ab<TT, false>(tile, c, 0u, f, h);
+        else
+            spull16ab<TT, true>(tile, c, bb, f, h);
+        ra = dens_hat(f);
+        rb = dens_hat(h);
     }
 }
 
@@ -320,10 +342,9 @@ __device__ __forceinline__ unsigned nb_bits(const uint8_t *sm, int mc,
 }
 
 // Tensor maps of one launch, per lattice: the tile copies (populations,
-// FP16 references and FP32 rest planes, mask) and the output stores.
+// mask) and the output stores.
 struct TmaMaps {
-    const CUtensorMap *pop, *mom, *rest, *mask;
-    const CUtensorMap *out, *out_mom, *out_rest;
+    const CUtensorMap *pop, *mask, *out;
 };
 
 template <class S, int TX, int TY>
@@ -334,12 +355,6 @@ __global__ void __launch_bounds__(TX *TY)
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem[];
     auto stage_pop = [&](int s) { return reinterpret_cast<T *>(smem + s * TT::STAGE); };
-    auto stage_mom = [&](int s) {
-        return reinterpret_cast<__half *>(smem + s * TT::STAGE + TT::POP_BYTES);
-    };
-    auto stage_rest = [&](int s) {
-        return reinterpret_cast<float *>(smem + s * TT::STAGE + TT::REST_OFF);
-    };
     auto stage_mask = [&](int s) { return smem + s * TT::STAGE + TT::MASK_OFF; };
     auto sdesc = [&](int slot) {
         return reinterpret_cast<LatDesc *>(smem + TT::DESC_OFF + 128 * slot);
@@ -374,10 +389,6 @@ __global__ void __launch_bounds__(TX *TY)
         mbar_expect_tx(&bar[s], TT::TX_BYTES + extra_tx);
         bulk_load(sdesc(slot), a.desc + l, 128, &bar[s]);
         tma_load_3d(stage_pop(s), &mp.pop[l], x0 - TT::XO, y0, 0, &bar[s]);
-        if constexpr (S::kHalf) {
-            tma_load_3d(stage_mom(s), &mp.mom[l], x0 - TT::XO, y0, 0, &bar[s]);
-            tma_load_3d(stage_rest(s), &mp.rest[l], x0 - TT::XO, y0, 0, &bar[s]);
-        }
         tma_load_2d(stage_mask(s), &mp.mask[l], x0 - TT::MXO, y0, &bar[s]);
     };
 
@@ -400,19 +411,12 @@ __global__ void __launch_bounds__(TX *TY)
     const MaskBits mb(t);
 
     // output tile in shared memory (TS): node lid = ly * TX + lx of plane q
-    // at sout[q * NT + lid]; FP16 references at smom_out[c * NT + lid], FP16
-    // rest populations at srest_out[c * NT + lid]
+    // at sout[q * NT + lid]
     T *sout = reinterpret_cast<T *>(smem + TT::OUT_OFF);
-    __half *smom_out = reinterpret_cast<__half *>(smem + TT::OUT_OFF + TT::OUT_POP);
-    float *srest_out = reinterpret_cast<float *>(smem + TT::OUT_OFF + TT::OUT_REST);
     // bulk tensor store of the output tile (thread 0; every thread fenced
     // its writes and passed a barrier since)
     auto store_out = [&](const TileRec &r) {
         tma_store_3d(&mp.out[r.lat], sout, r.x0, r.y0, 0);
-        if constexpr (S::kHalf) {
-            tma_store_3d(&mp.out_mom[r.lat], smom_out, r.x0, r.y0, 0);
-            tma_store_3d(&mp.out_rest[r.lat], srest_out, r.x0, r.y0, 0);
-        }
         bulk_commit();
     };
     TileRec prev{-1, 0, 0, 0};  // thread 0: the tile whose output awaits its store
@@ -454,8 +458,6 @@ __global__ void __launch_bounds__(TX *TY)
         // positions further out are never a node's neighbour
         const int n_act = min(TY, ny - ty0), m_act = min(TX, nx - tx0);
         T *tp = stage_pop(s);
-        __half *tm = stage_mom(s);
-        float *tr = stage_rest(s);
         uint8_t *sm = stage_mask(s);
 
         // own node: mask bits, pull, density
@@ -475,16 +477,27 @@ __global__ void __launch_bounds__(TX *TY)
         const unsigned snb = clean ? 0u : nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
         float fA[Q], fB[Q], g[QS];
         float *fr = srho(k & 1);
+        float ra = 0.f, rb = 0.f;
         {
-            float ra = 0.f, rb = 0.f;
             if (own_pull_fluid) {
-                spull22<S, TT>(tp, tm, tr, pc, bb, clean, fA, fB, g);
+                spull22<S, TT>(tp, pc, bb, clean, fA, fB, g);
+                if constexpr (S::kHalf) {
+                    ra = dens_hat(fA);
+                    rb = dens_hat(fB);
+                } else {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+                    for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+                }
             }
             const bool force_solid = s_own & mb.force;
-            fr[(ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : ra;
-            fr[TT::RX * TT::RY + (ly + 1) * TT::RX + lx + 1] = force_solid ? 0.f : rb;
+            const int fc = (ly + 1) * TT::RX + lx + 1;
+            if constexpr (S::kHalf) {
+                reinterpret_cast<float2 *>(fr)[fc] =
+                    force_solid ? make_float2(0.f, 0.f) : make_float2(ra, rb);
+            } else {
+                fr[fc] = force_solid ? 0.f : ra;
+                fr[TT::RX * TT::RY + fc] = force_solid ? 0.f : rb;
+            }
         }
         // ring of the density frame: the lanes of the first warps take
         // RW consecutive ring cells each (consecutive addresses, no
@@ -499,14 +512,19 @@ __global__ void __launch_bounds__(TX *TY)
                 else { ry = 1 + r - 2 * TT::RX - TY; rx = TT::RX - 1; }
                 const int rmc = (ry + 1) * TT::MBX + rx - 1 + TT::MXO;
                 const int rpc = (ry + 1) * TT::BX + rx - 1 + TT::XO;
-                float ra = 0.f, rb = 0.f;
+                float qa = 0.f, qb = 0.f;
                 if (!(sm[rmc] & mb.force)) {
                     // per lane: a warp-uniform choice here measured slower
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
-                    sdens<S, TT>(tp, tm, tr, rpc, rbb, rbb == 0u, ra, rb);
+                    sdens<S, TT>(tp, rpc, rbb, rbb == 0u, qa, qb);
                 }
-                fr[ry * TT::RX + rx] = ra;
-                fr[TT::RX * TT::RY + ry * TT::RX + rx] = rb;
+                const int fc = ry * TT::RX + rx;
+                if constexpr (S::kHalf) {
+                    reinterpret_cast<float2 *>(fr)[fc] = make_float2(qa, qb);
+                } else {
+                    fr[fc] = qa;
+                    fr[TT::RX * TT::RY + fc] = qb;
+                }
             }
         }
         fence_proxy_async();
@@ -533,29 +551,53 @@ __global__ void __launch_bounds__(TX *TY)
 
         if (active) {
             const int own = y * d.pitch + x;
+            const int lid = ly * TX + lx;
             if (s_own & mb.force) {
-                if (own_pull_fluid) retire_node(a, d, l, own, fA, fB, g);
+                if (own_pull_fluid) {
+                    if constexpr (S::kHalf)
+                        retire_node16(a, d, l, own, fA, fB, g);
+                    else
+                        retire_node(a, d, l, own, fA, fB, g);
+                }
                 const uint8_t nb = s_own | mb.next;
                 if (nb != s_own) mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, nb);
             } else {
-                float rAn[Q], rBn[Q];
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int fc = (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i);
-                    rAn[i] = fr[fc];
-                    rBn[i] = fr[TT::RX * TT::RY + fc];
-                }
                 const int ns = __popc(snb & 0x1Eu);
-                const int lid = ly * TX + lx;
-                const bool flagged = fluid_update<S>(
-                    a, d, l, t, x, y, own, fA, fB, g, rAn, rBn, snb, ns,
-                    [&](const float *pa, const float *pb, const float *pg) {
-                        if (ts_tile)
-                            store_tile22<S, TT::NT>(sout + lid, smom_out + lid,
-                                                    srest_out + lid, pa, pb, pg);
-                        else
-                            store_node22<S>(a, d, own, pa, pb, pg);
-                    });
+                bool flagged;
+                if constexpr (S::kHalf) {
+                    float2 nbv[Q];
+#pragma unroll
+                    for (int i = 1; i < Q; ++i)
+                        nbv[i] = reinterpret_cast<const float2 *>(fr)[
+                            (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i)];
+                    flagged = fluid_update16(
+                        a, d, l, t, x, y, own, fA, fB, g, ra, rb, nbv, snb, ns,
+                        [&](const uint32_t *v) {
+                            if (ts_tile)
+                                store_words16(sout + lid, TT::NT, v);
+                            else
+                                store_words16(static_cast<uint32_t *>(a.fout) +
+                                                  d.pop_off + own,
+                                              (int)d.plane, v);
+                        });
+                } else {
+                    float rAn[Q], rBn[Q];
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) {
+                        const int fc = (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i);
+                        rAn[i] = fr[fc];
+                        rBn[i] = fr[TT::RX * TT::RY + fc];
+                    }
+                    flagged = fluid_update(
+                        a, d, l, t, x, y, own, fA, fB, g, rAn, rBn, snb, ns,
+                        [&](const float *pa, const float *pb, const float *pg) {
+                            if (ts_tile)
+                                store22_f32(reinterpret_cast<float *>(sout) + lid,
+                                            TT::NT, pa, pb, pg);
+                            else
+                                store_node22(a, d, own, pa, pb, pg);
+                        });
+                }
                 if (flagged)
                     mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, s_own | mb.next);
             }
@@ -616,16 +658,11 @@ cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
 }
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
-                            const CUtensorMap *mom_maps,
-                            const CUtensorMap *rest_maps,
                             const CUtensorMap *mask_maps,
-                            const CUtensorMap *out_maps,
-                            const CUtensorMap *out_mom_maps,
-                            const CUtensorMap *out_rest_maps,
-                            const TileRec *sched, int nslots, int grid, int tx,
-                            int ty, bool half, int *err, cudaStream_t s) {
-    const TmaMaps mp{pop_maps, mom_maps, rest_maps, mask_maps,
-                     out_maps, out_mom_maps, out_rest_maps};
+                            const CUtensorMap *out_maps, const TileRec *sched,
+                            int nslots, int grid, int tx, int ty, bool half,
+                            int *err, cudaStream_t s) {
+    const TmaMaps mp{pop_maps, mask_maps, out_maps};
 #define LBM_TMA_CASE(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
         return half ? launch_tma_t<Store16, X, Y>(a, mp, sched, nslots, grid, \
@@ -637,10 +674,10 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
     return cudaErrorInvalidValue;
 }
 
-// Tensor map geometry must match TmaTile: box (TX + 2 XO) x (TY + 4) x
-// planes for populations and moments, (TX + 32) x (TY + 4) for the mask;
-// the output maps span the lattice itself with box TX x TY x planes.
-int tma_box_x(int tx, bool half) { return tx + 2 * (half ? 8 : 4); }
+// Tensor map geometry must match TmaTile: box (TX + 8) x (TY + 4) x
+// planes of 32-bit words for the populations, (TX + 32) x (TY + 4) for the
+// mask; the output maps span the lattice itself with box TX x TY x planes.
+int tma_box_x(int tx) { return tx + 8; }
 int tma_mask_box_x(int tx) { return tx + 32; }
 
 }  // namespace lbmk
