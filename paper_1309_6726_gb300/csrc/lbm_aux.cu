@@ -68,14 +68,13 @@ __device__ __forceinline__ void store_node(void *fout, const LatDesc &d,
                     v + 2 * Q);
         return;
     }
-    float fa[Q], fb[Q], gh[QS];
-    for (int i = 0; i < Q; ++i) {
-        fa[i] = __fdiv_rn(v[i], wq(i));
-        fb[i] = __fdiv_rn(v[Q + i], wq(i));
-    }
+    float2 f[Q];
+    float gh[QS];
+    for (int i = 0; i < Q; ++i)
+        f[i] = make_float2(__fdiv_rn(v[i], wq(i)), __fdiv_rn(v[Q + i], wq(i)));
     for (int k = 0; k < QS; ++k) gh[k] = 4.0f * v[2 * Q + k];
     uint32_t wv[NW16];
-    enc_node16(fa, fb, gh, wv);
+    enc_node16(f, gh, wv);
     store_words16(static_cast<uint32_t *>(fout) + d.pop_off + own, pl, wv);
 }
 

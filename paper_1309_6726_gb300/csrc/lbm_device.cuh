@@ -180,12 +180,26 @@ __device__ __forceinline__ __half2 bits_h2(uint32_t w) {
 __device__ __forceinline__ float dec16(float d, float ref) {
     return __fmaf_rn(d, kInvDevScale, ref);
 }
-// The A and B values of one direction from their packed deviations.
-__device__ __forceinline__ void dec_pair(uint32_t w, float ra, float rb,
-                                         float &fa, float &fb) {
-    const float2 d = __half22float2(bits_h2(w));
-    fa = dec16(d.x, ra);
-    fb = dec16(d.y, rb);
+// ---- packed FP32 pairs ------------------------------------------------------
+// The FP16 path carries the two fluid components side by side as
+// {A, B} float2 values and does their (identical) arithmetic with the
+// paired FP32 instructions of sm_100-family GPUs (one instruction, two
+// independent IEEE operations, each rounded as its scalar counterpart).
+__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b (the product by -1 is exact, so this is the rounded difference)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, f2s(-1.0f), a);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+}
+
+// The {A, B} values of one direction from their packed deviations and the
+// source's references {rho~_A, rho~_B}.
+__device__ __forceinline__ float2 dec_pair(uint32_t w, float2 ref) {
+    return fma2(__half22float2(bits_h2(w)), f2s(kInvDevScale), ref);
 }
 // Solute direction k from the word of its pair (k even: low half).
 __device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
@@ -193,25 +207,20 @@ __device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
     return dec16(__half2float((k & 1) ? __high2half(h) : __low2half(h)), ref);
 }
 
-// Encodes the scaled post-collision values of A and B (fa, fb: 9 each)
-// into the 8 direction words w[0..7] and the two references (mass-exact,
+// Encodes the scaled post-collision {A, B} values f[0..8] into the 8
+// direction words w[0..7] and the references {rho~_A, rho~_B} (mass-exact,
 // see above).
-__device__ __forceinline__ void enc_ab(const float fa[Q], const float fb[Q],
-                                       uint32_t w[8], float &ra, float &rb) {
-    const float na = -kDevScale * fa[0], nb = -kDevScale * fb[0];
-    float ea = 0.f, eb = 0.f;
+__device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8]) {
+    const float2 n = mul2(f2s(-kDevScale), f[0]);
+    float2 e = f2s(0.f);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const float da = __fmaf_rn(fa[i], kDevScale, na);
-        const float db = __fmaf_rn(fb[i], kDevScale, nb);
-        const __half2 h = __floats2half2_rn(da, db);
-        const float2 back = __half22float2(h);
-        ea = __fmaf_rn(wq(i), __fsub_rn(da, back.x), ea);
-        eb = __fmaf_rn(wq(i), __fsub_rn(db, back.y), eb);
+        const float2 dv = fma2(f[i], f2s(kDevScale), n);
+        const __half2 h = __floats2half2_rn(dv.x, dv.y);
+        e = fma2(f2s(wq(i)), sub2(dv, __half22float2(h)), e);
         w[i - 1] = h2_bits(h);
     }
-    ra = __fmaf_rn(ea, kInvDevScale, fa[0]);
-    rb = __fmaf_rn(eb, kInvDevScale, fb[0]);
+    return fma2(e, f2s(kInvDevScale), f[0]);
 }
 
 // Encodes the 4 scaled solute values into two words and the reference.
@@ -235,22 +244,23 @@ __device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
 
 // The 13 stored words of a node from its scaled post-collision values, in
 // plane order (8 direction pairs, 2 solute pairs, rho~_A, rho~_B, C~).
-__device__ __forceinline__ void enc_node16(const float fa[Q], const float fb[Q],
-                                           const float gh[QS], uint32_t v[NW16]) {
-    float ra, rb, rc;
-    enc_ab(fa, fb, v, ra, rb);
+__device__ __forceinline__ void enc_node16(const float2 f[Q], const float gh[QS],
+                                           uint32_t v[NW16]) {
+    float rc;
+    const float2 r = enc_ab(f, v);
     enc_sol(gh, v[W16_SOL], v[W16_SOL + 1], rc);
-    v[W16_REF] = __float_as_uint(ra);
-    v[W16_REF + 1] = __float_as_uint(rb);
+    v[W16_REF] = __float_as_uint(r.x);
+    v[W16_REF + 1] = __float_as_uint(r.y);
     v[W16_REF + 2] = __float_as_uint(rc);
 }
 
-// Density of a D2Q9 component from its scaled populations (the same
-// rounding everywhere it is formed: own nodes, ring cells, both kernels).
-__device__ __forceinline__ float dens_hat(const float f[Q]) {
-    const float s1 = __fadd_rn(__fadd_rn(f[1], f[3]), __fadd_rn(f[2], f[4]));
-    const float s5 = __fadd_rn(__fadd_rn(f[5], f[7]), __fadd_rn(f[6], f[8]));
-    return __fmaf_rn(wq(0), f[0], __fmaf_rn(wq(1), s1, __fmul_rn(wq(5), s5)));
+// Densities {rho_A, rho_B} from the scaled {A, B} populations (the same
+// rounding everywhere they are formed: own nodes, ring cells, both
+// kernels).
+__device__ __forceinline__ float2 dens2(const float2 f[Q]) {
+    const float2 s1 = add2(add2(f[1], f[3]), add2(f[2], f[4]));
+    const float2 s5 = add2(add2(f[5], f[7]), add2(f[6], f[8]));
+    return fma2(f2s(wq(0)), f[0], fma2(f2s(wq(1)), s1, mul2(f2s(wq(5)), s5)));
 }
 
 // Reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32, within

@@ -228,83 +228,122 @@ __device__ __forceinline__ bool fluid_update(
 
 // ---------------------------------------------------------------------------
 // FP16 storage: the same update on scaled populations f^_i = f_i / w_i and
-// g^_k = 4 g_k.
+// g^_k = 4 g_k, the two fluid components side by side as {A, B} pairs
+// (packed FP32 instructions, lbm_device.cuh).
 // ---------------------------------------------------------------------------
 
-// Momentum of a D2Q9 component from its scaled populations,
-// j = sum_i w_i f^_i e_i.
-__device__ __forceinline__ void mom_hat(const float f[Q], float &jx,
-                                        float &jy) {
-    const float d57 = __fsub_rn(f[5], f[7]);
-    jx = __fmaf_rn(wq(1), __fsub_rn(f[1], f[3]),
-                   __fmul_rn(wq(5), __fadd_rn(d57, __fsub_rn(f[8], f[6]))));
-    jy = __fmaf_rn(wq(1), __fsub_rn(f[2], f[4]),
-                   __fmul_rn(wq(5), __fadd_rn(d57, __fsub_rn(f[6], f[8]))));
+// Momenta {j_A, j_B} from scaled populations, j = sum_i w_i f^_i e_i.
+__device__ __forceinline__ void mom2(const float2 f[Q], float2 &jx,
+                                     float2 &jy) {
+    const float2 d57 = sub2(f[5], f[7]);
+    jx = fma2(f2s(wq(1)), sub2(f[1], f[3]),
+              mul2(f2s(wq(5)), add2(d57, sub2(f[8], f[6]))));
+    jy = fma2(f2s(wq(1)), sub2(f[2], f[4]),
+              mul2(f2s(wq(5)), add2(d57, sub2(f[6], f[8]))));
 }
 
-// BGK relaxation of scaled populations towards
+// sum_i w_i v(x + e_i) e_i for eight neighbour pairs v[1..8].
+__device__ __forceinline__ void stencil2(const float2 v[Q], float2 &sx_,
+                                         float2 &sy_) {
+    const float2 d1 = sub2(v[5], v[7]), d2 = sub2(v[8], v[6]);
+    sx_ = fma2(f2s(wq(1)), sub2(v[1], v[3]), mul2(f2s(wq(5)), add2(d1, d2)));
+    sy_ = fma2(f2s(wq(1)), sub2(v[2], v[4]), mul2(f2s(wq(5)), sub2(d1, d2)));
+}
+
+// BGK relaxation of scaled {A, B} populations towards
 //   f^eq_i = rho (1 + 3 e_i.u + 9/2 (e_i.u)^2 - 3/2 u.u),
-// pairwise as bgk9.  The rest value closes the mass exactly as dens_hat
-// forms it: w_0 f^eq_0 = rho - (w_1 S_1 + w_5 S_5), the quotient by the
-// FP32 w_0 taken as a product with 9/4 and one fused multiply-add
-// correction (9/4 alone would make w_0 f^eq_0 exceed its target by 7e-9,
-// mass created at every collision).
-__device__ __forceinline__ void bgk9_hat(float f[Q], float rho, float ux,
-                                         float uy, float omega) {
-    const float a = rho * (1.0f - 1.5f * (ux * ux + uy * uy));
-    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-    const float up = ux + uy, um = ux - uy;
-    const float sx_ = a + r45 * ux * ux, sy_ = a + r45 * uy * uy;
-    const float sp = a + r45 * up * up, sm = a + r45 * um * um;
-    const float px = r3 * ux, py = r3 * uy, pp = r3 * up, pm = r3 * um;
-    float feq[Q];
-    feq[1] = sx_ + px;
-    feq[3] = sx_ - px;
-    feq[2] = sy_ + py;
-    feq[4] = sy_ - py;
-    feq[5] = sp + pp;   // (1, 1)
-    feq[7] = sp - pp;   // (-1, -1)
-    feq[8] = sm + pm;   // (1, -1)
-    feq[6] = sm - pm;   // (-1, 1)
-    const float s1 = __fadd_rn(__fadd_rn(feq[1], feq[3]), __fadd_rn(feq[2], feq[4]));
-    const float s5 = __fadd_rn(__fadd_rn(feq[5], feq[7]), __fadd_rn(feq[6], feq[8]));
-    const float v = __fsub_rn(rho, __fmaf_rn(wq(1), s1, __fmul_rn(wq(5), s5)));
-    const float y0 = __fmul_rn(v, 2.25f);
-    feq[0] = __fmaf_rn(__fmaf_rn(-wq(0), y0, v), 2.25f, y0);
+// pairwise as bgk9.  The rest value closes the mass exactly as dens2 forms
+// it: w_0 f^eq_0 = rho - (w_1 S_1 + w_5 S_5), the quotient by the FP32 w_0
+// taken as a product with 9/4 and one fused multiply-add correction (9/4
+// alone would make w_0 f^eq_0 exceed its target by 7e-9, mass created at
+// every collision).
+__device__ __forceinline__ void bgk2(float2 f[Q], float2 rho, float2 ux,
+                                     float2 uy, float2 omega) {
+    const float2 uu = fma2(ux, ux, mul2(uy, uy));
+    const float2 a = mul2(rho, fma2(f2s(-1.5f), uu, f2s(1.0f)));
+    const float2 r3 = mul2(f2s(3.0f), rho), r45 = mul2(f2s(4.5f), rho);
+    const float2 up = add2(ux, uy), um = sub2(ux, uy);
+    const float2 sx_ = fma2(mul2(r45, ux), ux, a), sy_ = fma2(mul2(r45, uy), uy, a);
+    const float2 sp = fma2(mul2(r45, up), up, a), sm = fma2(mul2(r45, um), um, a);
+    const float2 px = mul2(r3, ux), py = mul2(r3, uy);
+    const float2 pp = mul2(r3, up), pm = mul2(r3, um);
+    float2 feq[Q];
+    feq[1] = add2(sx_, px);
+    feq[3] = sub2(sx_, px);
+    feq[2] = add2(sy_, py);
+    feq[4] = sub2(sy_, py);
+    feq[5] = add2(sp, pp);   // (1, 1)
+    feq[7] = sub2(sp, pp);   // (-1, -1)
+    feq[8] = add2(sm, pm);   // (1, -1)
+    feq[6] = sub2(sm, pm);   // (-1, 1)
+    const float2 s1 = add2(add2(feq[1], feq[3]), add2(feq[2], feq[4]));
+    const float2 s5 = add2(add2(feq[5], feq[7]), add2(feq[6], feq[8]));
+    const float2 v = sub2(rho, fma2(f2s(wq(1)), s1, mul2(f2s(wq(5)), s5)));
+    const float2 y0 = mul2(v, f2s(2.25f));
+    feq[0] = fma2(fma2(f2s(-wq(0)), y0, v), f2s(2.25f), y0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = f[i] + omega * (feq[i] - f[i]);
+    for (int i = 0; i < Q; ++i) f[i] = fma2(omega, sub2(feq[i], f[i]), f[i]);
+}
+
+// 1 / x by the hardware approximation and one Newton-Raphson step, for a
+// pair, 0 where x <= lim (as rcp_nr).
+__device__ __forceinline__ float2 rcp2_guard(float2 x, float lim) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.y));
+    const float2 e = fma2(make_float2(-x.x, -x.y), r, f2s(1.0f));
+    r = fma2(r, e, r);
+    return make_float2(x.x > lim ? r.x : 0.f, x.y > lim ? r.y : 0.f);
 }
 
 // Everything after the pull for a node fluid in s_t, FP16 storage.
-//   fA, fB, g: scaled post-streaming populations of the node;
-//   rA, rB: its densities (dens_hat of fA, fB, as in the density frame);
+//   f, g: scaled post-streaming {A, B} populations and solute of the node;
+//   rho: its densities {rho_A, rho_B} (dens2 of f, as in the density frame);
 //   nb: densities {rho_A, rho_B} at x + e_i (index 1..8; 0 if solid);
 //   snb, ns: as for fluid_update.
-// put(words) writes the node's 13 stored words; its periodic images in the
-// ghost band are written here.  Returns true if the node reached the
-// threshold in this step.
+// The forces and the shift are those of forces_shift (readings c1, c3, c4),
+// formed for both components at once.  put(words) writes the node's 13
+// stored words; its periodic images in the ghost band are written here.
+// Returns true if the node reached the threshold in this step.
 template <class Put>
 __device__ __forceinline__ bool fluid_update16(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
-    int own, float fA[Q], float fB[Q], float g[QS], float rA, float rB,
-    const float2 nb[Q], unsigned snb, int ns, Put put) {
-    float jAx, jAy, jBx, jBy;
-    mom_hat(fA, jAx, jAy);
-    mom_hat(fB, jBx, jBy);
-    float nA[Q], nB[Q];
+    int own, float2 f[Q], float g[QS], float2 rho, const float2 nb[Q],
+    unsigned snb, int ns, Put put) {
+    float2 jx, jy;
+    mom2(f, jx, jy);
+    // ---- Martys-Chen forces: A feels B, B feels A -------------------------
+    float2 sw[Q];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        nA[i] = nb[i].x;
-        nB[i] = nb[i].y;
+    for (int i = 1; i < Q; ++i) sw[i] = make_float2(nb[i].y, nb[i].x);
+    float2 cx2, cy2;
+    stencil2(sw, cx2, cy2);
+    float adx = 0.f, ady = 0.f;
+    if (snb != 0u) {  // solid neighbours: adhesion stencil
+        float sv[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) sv[i] = ((snb >> i) & 1u) ? 1.f : 0.f;
+        stencil9(sv, adx, ady);
     }
-    const Shift sh = forces_shift(d, rA, rB, jAx, jAy, jBx, jBy, nA, nB, snb);
-    bgk9_hat(fA, rA, sh.upx + sh.sA * sh.FAx, sh.upy + sh.sA * sh.FAy, d.inv_tau_a);
-    bgk9_hat(fB, rB, sh.upx + sh.sB * sh.FBx, sh.upy + sh.sB * sh.FBy, d.inv_tau_b);
+    // G_ads,A = -g_ads, G_ads,B = +g_ads
+    const float2 gx2 = make_float2(d.g_ads * adx + d.body_x, -d.g_ads * adx + d.body_x);
+    const float2 gy2 = make_float2(d.g_ads * ady, -d.g_ads * ady);
+    const float2 Fx = mul2(rho, fma2(f2s(-d.g_coh), cx2, gx2));
+    const float2 Fy = mul2(rho, fma2(f2s(-d.g_coh), cy2, gy2));
+    // ---- Shan-Chen shift and BGK -----------------------------------------
+    const float2 itau = make_float2(d.inv_tau_a, d.inv_tau_b);
+    const float2 tau = make_float2(d.tau_a, d.tau_b);
+    const float2 rw = mul2(rho, itau), jxw = mul2(jx, itau), jyw = mul2(jy, itau);
+    const float den = rw.x + rw.y;
+    const float iden = den > 1e-30f ? rcp_nr(den) : 0.f;
+    const float upx = (jxw.x + jxw.y) * iden, upy = (jyw.x + jyw.y) * iden;
+    const float2 sh = mul2(tau, rcp2_guard(rho, 1e-12f));
+    bgk2(f, rho, fma2(sh, Fx, f2s(upx)), fma2(sh, Fy, f2s(upy)), itau);
     // ---- solute (scaled: g^eq_k = C (1 + 2 e_k.u), C = sum_k g^_k / 4) --
-    const float rt = rA + rB;
+    const float rt = rho.x + rho.y;
     const float irt = rt > 1e-30f ? rcp_nr(rt) : 0.f;
-    const float ux = ((jAx + jBx) + 0.5f * (sh.FAx + sh.FBx)) * irt;
-    const float uy = ((jAy + jBy) + 0.5f * (sh.FAy + sh.FBy)) * irt;
+    const float ux = ((jx.x + jx.y) + 0.5f * (Fx.x + Fx.y)) * irt;
+    const float uy = ((jy.x + jy.y) + 0.5f * (Fy.x + Fy.y)) * irt;
     {
         const bool inl = d.inlet && gx == 0;
         const float c = inl ? d.c_in : 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
@@ -316,7 +355,7 @@ __device__ __forceinline__ bool fluid_update16(
     }
     // ---- surface reaction, deposit, threshold ----------------------------
     bool flagged = false;
-    if (ns > 0 && rA > rB) {
+    if (ns > 0 && rho.x > rho.y) {
         const float cs = 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
         const float lost = fminf(1.0f, d.k_r * (float)ns);
 #pragma unroll
@@ -335,7 +374,7 @@ __device__ __forceinline__ bool fluid_update16(
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
     uint32_t v[NW16];
-    enc_node16(fA, fB, g, v);
+    enc_node16(f, g, v);
     put(v);
     // periodic images in the ghost band
     uint32_t *out = static_cast<uint32_t *>(a.fout) + d.pop_off;
@@ -348,14 +387,13 @@ __device__ __forceinline__ bool fluid_update16(
 // post-streaming content (weights applied) and its deposit to the ledger.
 __device__ __forceinline__ void retire_node16(const StepArgs &a,
                                               const LatDesc &d, int l,
-                                              int own, const float fA[Q],
-                                              const float fB[Q],
+                                              int own, const float2 f[Q],
                                               const float g[QS]) {
     double ra = 0, rb = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        ra += (double)wq(i) * fA[i];
-        rb += (double)wq(i) * fB[i];
+        ra += (double)wq(i) * f[i].x;
+        rb += (double)wq(i) * f[i].y;
     }
     const double c = 0.25 * ((double)g[0] + g[1] + g[2] + g[3]);
     double *mp = a.m + d.node_off + own;

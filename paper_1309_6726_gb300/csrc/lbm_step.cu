@@ -83,18 +83,16 @@ __device__ __forceinline__ void pull4(const float *__restrict__ fin,
     }
 }
 
-// FP16 storage: the scaled A and B populations pulled into node (gx, gy)
+// FP16 storage: the scaled {A, B} populations pulled into node (gx, gy)
 // (bb: bounce-back bits of the 9 directions).
 __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
                                          const LatDesc &d, int gx, int gxm,
                                          int gxp, int gy, int gym, int gyp,
-                                         unsigned bb, float fA[Q],
-                                         float fB[Q]) {
+                                         unsigned bb, float2 f[Q]) {
     const uint32_t *w = fin + d.pop_off;
     const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
     const int64_t own = (int64_t)gy * d.pitch + gx;
-    fA[0] = __ldg(ref + own);
-    fB[0] = __ldg(ref + d.plane + own);
+    f[0] = make_float2(__ldg(ref + own), __ldg(ref + d.plane + own));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int sxx = cx(i) > 0 ? gxm : (cx(i) < 0 ? gxp : gx);
@@ -102,8 +100,8 @@ __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
         const bool b = (bb >> i) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
         const int qi = b ? opp(i) : i;
-        dec_pair(__ldg(w + (qi - 1) * d.plane + src), __ldg(ref + src),
-                 __ldg(ref + d.plane + src), fA[i], fB[i]);
+        f[i] = dec_pair(__ldg(w + (qi - 1) * d.plane + src),
+                        make_float2(__ldg(ref + src), __ldg(ref + d.plane + src)));
     }
 }
 
@@ -128,27 +126,27 @@ __device__ __forceinline__ void pull16s(const uint32_t *__restrict__ fin,
     }
 }
 
-// Both components' populations (scaled for FP16) and their densities, as
-// the TMA kernel forms them.
+// Both components' populations and their densities {rho_A, rho_B}, as the
+// TMA kernel forms them: FP32 storage into fA, fB; FP16 storage as scaled
+// {A, B} pairs into f2.
 template <class S>
-__device__ __forceinline__ void pull_ab(const StepArgs &a, const LatDesc &d,
-                                        int gx, int gxm, int gxp, int gy,
-                                        int gym, int gyp, unsigned bb,
-                                        float fA[Q], float fB[Q], float &ra,
-                                        float &rb) {
+__device__ __forceinline__ float2 pull_ab(const StepArgs &a, const LatDesc &d,
+                                          int gx, int gxm, int gxp, int gy,
+                                          int gym, int gyp, unsigned bb,
+                                          float fA[Q], float fB[Q],
+                                          float2 f2[Q]) {
     if constexpr (!S::kHalf) {
         const float *fin = static_cast<const float *>(a.fin);
         pull9(fin, d, 0, gx, gxm, gxp, gy, gym, gyp, bb, fA);
         pull9(fin, d, 1, gx, gxm, gxp, gy, gym, gyp, bb, fB);
-        ra = 0.f;
-        rb = 0.f;
+        float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+        return make_float2(ra, rb);
     } else {
         pull16ab(static_cast<const uint32_t *>(a.fin), d, gx, gxm, gxp, gy,
-                 gym, gyp, bb, fA, fB);
-        ra = dens_hat(fA);
-        rb = dens_hat(fB);
+                 gym, gyp, bb, f2);
+        return dens2(f2);
     }
 }
 
@@ -202,15 +200,16 @@ __global__ void __launch_bounds__(TX *TY)
     const uint8_t s_own = smask[ly + 2][lx + 2];
     const bool own_pull_fluid = !(s_own & mb.pull);
     float fA[Q], fB[Q];
-    float ra = 0.f, rb = 0.f;
+    float2 f2[Q];  // FP16 storage: scaled {A, B} pairs
+    float2 rho = make_float2(0.f, 0.f);
     {
         if (own_pull_fluid) {
             const unsigned bb = pull_bits<TL::HX>(smask, ly + 2, lx + 2, mb.pull);
-            pull_ab<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb, fA, fB, ra, rb);
+            rho = pull_ab<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb, fA, fB, f2);
         }
         const bool force_solid = s_own & mb.force;
-        srho[0][ly + 1][lx + 1] = force_solid ? 0.f : ra;
-        srho[1][ly + 1][lx + 1] = force_solid ? 0.f : rb;
+        srho[0][ly + 1][lx + 1] = force_solid ? 0.f : rho.x;
+        srho[1][ly + 1][lx + 1] = force_solid ? 0.f : rho.y;
     }
     // --- ring of the density frame ----------------------------------------
     for (int r = tid; r < TL::NRING; r += TL::NT) {
@@ -220,17 +219,18 @@ __global__ void __launch_bounds__(TX *TY)
         else if (r < 2 * TL::RX + TY) { ry = 1 + r - 2 * TL::RX; rx = 0; }
         else { ry = 1 + r - 2 * TL::RX - TY; rx = TL::RX - 1; }
         const uint8_t s = smask[ry + 1][rx + 1];
-        float qa = 0.f, qb = 0.f;
+        float2 q = make_float2(0.f, 0.f);
         if (!(s & mb.force)) {
             const int X = wrapg(tx0 - 1 + rx, nx), Y = wrapg(ty0 - 1 + ry, ny);
             const int Xm = wrap1(X - 1, nx), Xp = wrap1(X + 1, nx);
             const int Ym = wrap1(Y - 1, ny), Yp = wrap1(Y + 1, ny);
             const unsigned bb = pull_bits<TL::HX>(smask, ry + 1, rx + 1, mb.pull);
             float f[Q], h[Q];
-            pull_ab<S>(a, d, X, Xm, Xp, Y, Ym, Yp, bb, f, h, qa, qb);
+            float2 p2[Q];
+            q = pull_ab<S>(a, d, X, Xm, Xp, Y, Ym, Yp, bb, f, h, p2);
         }
-        srho[0][ry][rx] = qa;
-        srho[1][ry][rx] = qb;
+        srho[0][ry][rx] = q.x;
+        srho[1][ry][rx] = q.y;
     }
     __syncthreads();
 
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(TX *TY)
                 float g[QS];
                 pull_sol<S>(a, d, gx, gxm, gxp, gy, gym, gyp, bb4, g);
                 if constexpr (S::kHalf)
-                    retire_node16(a, d, l, own, fA, fB, g);
+                    retire_node16(a, d, l, own, f2, g);
                 else
                     retire_node(a, d, l, own, fA, fB, g);
             }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(TX *TY)
 #pragma unroll
                 for (int i = 1; i < Q; ++i) nbv[i] = make_float2(rAn[i], rBn[i]);
                 flagged = fluid_update16(
-                    a, d, l, t, gx, gy, own, fA, fB, g, ra, rb, nbv, snb, ns,
+                    a, d, l, t, gx, gy, own, f2, g, rho, nbv, snb, ns,
                     [&](const uint32_t *v) {
                         store_words16(static_cast<uint32_t *>(a.fout) + d.pop_off + own,
                                       (int)d.plane, v);

@@ -166,11 +166,17 @@ struct TmaTile {
     static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
     static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
     // The tile's post-collision output, [NPL][TY][TX] words, written by
-    // bulk tensor stores -- where it fits.
+    // bulk tensor stores -- where it fits.  FP16 tiles keep two output
+    // tiles where they fit (ONE_BAR): the store of one tile is issued while
+    // the next is written, which leaves one block barrier per tile instead
+    // of two.
     static constexpr int OUT_BYTES = (NPL * NT * 4 + 127) / 128 * 128;
     static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
     static constexpr bool TS = OUT_OFF + OUT_BYTES + 128 <= 232448;
-    static constexpr int BAR_OFF = OUT_OFF + (TS ? OUT_BYTES : 0);
+    static constexpr bool ONE_BAR =
+        S::kHalf && OUT_OFF + 2 * OUT_BYTES + 128 <= 232448;
+    static constexpr int NOUT = ONE_BAR ? 2 : (TS ? 1 : 0);
+    static constexpr int BAR_OFF = OUT_OFF + NOUT * OUT_BYTES;
     static constexpr int SMEM = BAR_OFF + 128;
     static_assert(SMEM <= 232448, "shared memory per block");
     static_assert((TX * 4) % 16 == 0, "store box row");
@@ -210,23 +216,21 @@ __device__ __forceinline__ void spull4(const float *tile, int c, unsigned bb4,
     }
 }
 
-// FP16 storage: the scaled A and B populations pulled into the node at
+// FP16 storage: the scaled {A, B} populations pulled into the node at
 // stage cell c -- one packed word and the source's two FP32 references per
 // direction; the rest populations are the node's own references.
 template <class TT, bool BB>
 __device__ __forceinline__ void spull16ab(const uint32_t *tile, int c,
-                                          unsigned bb, float fA[Q],
-                                          float fB[Q]) {
+                                          unsigned bb, float2 f[Q]) {
     const float *ref = reinterpret_cast<const float *>(tile) + W16_REF * TT::PL;
-    fA[0] = ref[c];
-    fB[0] = ref[TT::PL + c];
+    f[0] = make_float2(ref[c], ref[TT::PL + c]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const bool b = BB && ((bb >> i) & 1u);
         const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
         const int qi = b ? opp(i) : i;
-        dec_pair(tile[(qi - 1) * TT::PL + cell], ref[cell], ref[TT::PL + cell],
-                 fA[i], fB[i]);
+        f[i] = dec_pair(tile[(qi - 1) * TT::PL + cell],
+                        make_float2(ref[cell], ref[TT::PL + cell]));
     }
 }
 
@@ -245,14 +249,16 @@ __device__ __forceinline__ void spull16s(const uint32_t *tile, int c,
     }
 }
 
-// The 22 populations of the node at stage cell c (scaled for FP16).
-// `fast` (bb == 0 on every lane that calls) takes the path without
-// bounce-back selects; the other path gives the same values for bb == 0,
-// so a warp with any bounce-back lane runs that one alone.
+// The 22 populations of the node at stage cell c, FP32 storage (fA, fB, g)
+// or FP16 storage (scaled {A, B} pairs in fA2, solute in g).  `fast`
+// (bb == 0 on every lane that calls) takes the path without bounce-back
+// selects; the other path gives the same values for bb == 0, so a warp with
+// any bounce-back lane runs that one alone.
 template <class S, class TT>
 __device__ __forceinline__ void spull22(const typename S::T *tile, int c,
                                         unsigned bb, bool fast, float fA[Q],
-                                        float fB[Q], float g[QS]) {
+                                        float fB[Q], float2 fA2[Q],
+                                        float g[QS]) {
     if constexpr (!S::kHalf) {
         if (fast) {
             spull9<TT, false>(tile, 0, c, 0u, fA);
@@ -265,10 +271,10 @@ __device__ __forceinline__ void spull22(const typename S::T *tile, int c,
         }
     } else {
         if (fast) {
-            spull16ab<TT, false>(tile, c, 0u, fA, fB);
+            spull16ab<TT, false>(tile, c, 0u, fA2);
             spull16s<TT, false>(tile, c, 0u, g);
         } else {
-            spull16ab<TT, true>(tile, c, bb, fA, fB);
+            spull16ab<TT, true>(tile, c, bb, fA2);
             spull16s<TT, true>(tile, c, bb, g);
         }
     }
@@ -277,13 +283,11 @@ __device__ __forceinline__ void spull22(const typename S::T *tile, int c,
 // Densities of both components at stage cell c (`fast` as for spull22),
 // formed as the node's own update forms them.
 template <class S, class TT>
-__device__ __forceinline__ void sdens(const typename S::T *tile, int c,
-                                      unsigned bb, bool fast, float &ra,
-                                      float &rb) {
-    float f[Q], h[Q];
+__device__ __forceinline__ float2 sdens(const typename S::T *tile, int c,
+                                        unsigned bb, bool fast) {
     if constexpr (!S::kHalf) {
-        ra = 0.f;
-        rb = 0.f;
+        float f[Q];
+        float ra = 0.f, rb = 0.f;
         if (fast) {
             spull9<TT, false>(tile, 0, c, 0u, f);
 #pragma unroll
@@ -299,13 +303,14 @@ __device__ __forceinline__ void sdens(const typename S::T *tile, int c,
 #pragma unroll
             for (int i = 0; i < Q; ++i) rb += f[i];
         }
+        return make_float2(ra, rb);
     } else {
+        float2 f[Q];
         if (fast)
-            spull16ab<TT, false>(tile, c, 0u, f, h);
+            spull16ab<TT, false>(tile, c, 0u, f);
         else
-            spull16ab<TT, true>(tile, c, bb, f, h);
-        ra = dens_hat(f);
-        rb = dens_hat(h);
+            spull16ab<TT, true>(tile, c, bb, f);
+        return dens2(f);
     }
 }
 
@@ -410,17 +415,34 @@ __global__ void __launch_bounds__(TX *TY)
     const long long t = *s_t;
     const MaskBits mb(t);
 
-    // output tile in shared memory (TS): node lid = ly * TX + lx of plane q
-    // at sout[q * NT + lid]
-    T *sout = reinterpret_cast<T *>(smem + TT::OUT_OFF);
-    // bulk tensor store of the output tile (thread 0; every thread fenced
-    // its writes and passed a barrier since)
-    auto store_out = [&](const TileRec &r) {
-        tma_store_3d(&mp.out[r.lat], sout, r.x0, r.y0, 0);
+    // output tiles in shared memory (TS): node lid = ly * TX + lx of plane q
+    // at sout(b)[q * NT + lid]
+    auto sout = [&](int b) {
+        return reinterpret_cast<T *>(smem + TT::OUT_OFF +
+                                     (TT::NOUT == 2 ? (b & 1) : 0) * TT::OUT_BYTES);
+    };
+    // bulk tensor store of output tile b (thread 0; every thread fenced its
+    // writes and passed a barrier since)
+    auto store_out = [&](const TileRec &r, int b) {
+        tma_store_3d(&mp.out[r.lat], sout(b), r.x0, r.y0, 0);
         bulk_commit();
     };
-    TileRec prev{-1, 0, 0, 0};  // thread 0: the tile whose output awaits its store
+    // thread 0: the tile whose output awaits its store, and its output tile
+    TileRec prev{-1, 0, 0, 0};
+    int prev_buf = 0;
     bool failed = false;
+    // gives up after a bounded wait ran out: lets the copies still in
+    // flight land before exiting
+    auto give_up = [&](int k, unsigned par) {
+        if (tid == 0) {
+            atomicOr(err, 1);
+            for (int j = 1; j < NS; ++j) {
+                if (s_rec[(k + j) % NSL].lat < 0) break;
+                const int sj = (k + j) % NS;
+                mbar_wait_bounded(&bar[sj], (par >> sj) & 1u);
+            }
+        }
+    };
 
     unsigned parity = 0u;  // bit s: phase parity of stage s
     for (int k = 0; s_rec[k % NSL].lat >= 0; ++k) {
@@ -432,23 +454,18 @@ __global__ void __launch_bounds__(TX *TY)
         const int slot = k % NSL;
         const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
         parity ^= 1u << s;
-        if (__syncthreads_or(!ok)) {
-            // give up: let the copies still in flight land before exiting
-            if (tid == 0) {
-                atomicOr(err, 1);
-                for (int j = 1; j < NS; ++j) {
-                    if (s_rec[(k + j) % NSL].lat < 0) break;
-                    const int sj = (k + j) % NS;
-                    mbar_wait_bounded(&bar[sj], (parity >> sj) & 1u);
-                }
+        if constexpr (!TT::ONE_BAR) {
+            if (__syncthreads_or(!ok)) {
+                give_up(k, parity);
+                failed = true;
+                break;
             }
-            failed = true;
-            break;
-        }
-        if constexpr (TT::TS) {
             // every thread finished the previous tile's output
-            if (tid == 0 && prev.lat >= 0) store_out(prev);
+            if (TT::TS && tid == 0 && prev.lat >= 0) store_out(prev, 0);
         }
+        // (ONE_BAR: a thread whose wait ran out still reads the stage --
+        // shared memory at fixed offsets, results discarded -- and the
+        // failure is taken at the barrier below)
         const TileRec rc = s_rec[slot];
         const LatDesc &d = *sdesc(slot);
         const int l = rc.lat;
@@ -476,27 +493,27 @@ __global__ void __launch_bounds__(TX *TY)
         const unsigned bb = clean ? 0u : nb_bits<TT, -1>(sm, mc, mb.pull);   // sources solid
         const unsigned snb = clean ? 0u : nb_bits<TT, +1>(sm, mc, mb.force); // neighbours solid
         float fA[Q], fB[Q], g[QS];
+        float2 f2[Q];  // FP16 storage: scaled {A, B} pairs
         float *fr = srho(k & 1);
-        float ra = 0.f, rb = 0.f;
+        float2 rho = make_float2(0.f, 0.f);
         {
             if (own_pull_fluid) {
-                spull22<S, TT>(tp, pc, bb, clean, fA, fB, g);
+                spull22<S, TT>(tp, pc, bb, clean, fA, fB, f2, g);
                 if constexpr (S::kHalf) {
-                    ra = dens_hat(fA);
-                    rb = dens_hat(fB);
+                    rho = dens2(f2);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
+                    for (int i = 0; i < Q; ++i) { rho.x += fA[i]; rho.y += fB[i]; }
                 }
             }
             const bool force_solid = s_own & mb.force;
             const int fc = (ly + 1) * TT::RX + lx + 1;
             if constexpr (S::kHalf) {
                 reinterpret_cast<float2 *>(fr)[fc] =
-                    force_solid ? make_float2(0.f, 0.f) : make_float2(ra, rb);
+                    force_solid ? make_float2(0.f, 0.f) : rho;
             } else {
-                fr[fc] = force_solid ? 0.f : ra;
-                fr[TT::RX * TT::RY + fc] = force_solid ? 0.f : rb;
+                fr[fc] = force_solid ? 0.f : rho.x;
+                fr[TT::RX * TT::RY + fc] = force_solid ? 0.f : rho.y;
             }
         }
         // ring of the density frame: the lanes of the first warps take
@@ -512,18 +529,18 @@ __global__ void __launch_bounds__(TX *TY)
                 else { ry = 1 + r - 2 * TT::RX - TY; rx = TT::RX - 1; }
                 const int rmc = (ry + 1) * TT::MBX + rx - 1 + TT::MXO;
                 const int rpc = (ry + 1) * TT::BX + rx - 1 + TT::XO;
-                float qa = 0.f, qb = 0.f;
+                float2 q = make_float2(0.f, 0.f);
                 if (!(sm[rmc] & mb.force)) {
                     // per lane: a warp-uniform choice here measured slower
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
-                    sdens<S, TT>(tp, rpc, rbb, rbb == 0u, qa, qb);
+                    q = sdens<S, TT>(tp, rpc, rbb, rbb == 0u);
                 }
                 const int fc = ry * TT::RX + rx;
                 if constexpr (S::kHalf) {
-                    reinterpret_cast<float2 *>(fr)[fc] = make_float2(qa, qb);
+                    reinterpret_cast<float2 *>(fr)[fc] = q;
                 } else {
-                    fr[fc] = qa;
-                    fr[TT::RX * TT::RY + fc] = qb;
+                    fr[fc] = q.x;
+                    fr[TT::RX * TT::RY + fc] = q.y;
                 }
             }
         }
@@ -535,14 +552,26 @@ __global__ void __launch_bounds__(TX *TY)
         // those tiles store their nodes directly.
         const bool ts_tile = TT::TS && tx0 + TX <= nx;
         if constexpr (TT::TS) {
-            // the output tile is rewritten below: its last store must have
-            // read it
-            if (tid == 0) {
-                bulk_wait_read();
-                prev = ts_tile ? rc : TileRec{-1, 0, 0, 0};
-            }
+            // the output tile written below must have been read by its last
+            // store (ONE_BAR: the store of two tiles ago)
+            if (tid == 0) bulk_wait_read();
         }
-        __syncthreads();
+        if constexpr (TT::ONE_BAR) {
+            if (__syncthreads_or(!ok)) {
+                give_up(k, parity);
+                failed = true;
+                break;
+            }
+            // every thread finished the previous tile's output
+            if (tid == 0) {
+                if (prev.lat >= 0) store_out(prev, prev_buf);
+                prev = ts_tile ? rc : TileRec{-1, 0, 0, 0};
+                prev_buf = k & 1;
+            }
+        } else {
+            if (TT::TS && tid == 0) prev = ts_tile ? rc : TileRec{-1, 0, 0, 0};
+            __syncthreads();
+        }
         // stage s is free: start the copy of the tile NS ahead into it
         if (tid == 0) {
             s_rec[(k + NS) % NSL] = nxt;
@@ -555,7 +584,7 @@ __global__ void __launch_bounds__(TX *TY)
             if (s_own & mb.force) {
                 if (own_pull_fluid) {
                     if constexpr (S::kHalf)
-                        retire_node16(a, d, l, own, fA, fB, g);
+                        retire_node16(a, d, l, own, f2, g);
                     else
                         retire_node(a, d, l, own, fA, fB, g);
                 }
@@ -571,10 +600,10 @@ __global__ void __launch_bounds__(TX *TY)
                         nbv[i] = reinterpret_cast<const float2 *>(fr)[
                             (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i)];
                     flagged = fluid_update16(
-                        a, d, l, t, x, y, own, fA, fB, g, ra, rb, nbv, snb, ns,
+                        a, d, l, t, x, y, own, f2, g, rho, nbv, snb, ns,
                         [&](const uint32_t *v) {
                             if (ts_tile)
-                                store_words16(sout + lid, TT::NT, v);
+                                store_words16(sout(k) + lid, TT::NT, v);
                             else
                                 store_words16(static_cast<uint32_t *>(a.fout) +
                                                   d.pop_off + own,
@@ -592,7 +621,7 @@ __global__ void __launch_bounds__(TX *TY)
                         a, d, l, t, x, y, own, fA, fB, g, rAn, rBn, snb, ns,
                         [&](const float *pa, const float *pb, const float *pg) {
                             if (ts_tile)
-                                store22_f32(reinterpret_cast<float *>(sout) + lid,
+                                store22_f32(reinterpret_cast<float *>(sout(k)) + lid,
                                             TT::NT, pa, pb, pg);
                             else
                                 store_node22(a, d, own, pa, pb, pg);
@@ -607,7 +636,7 @@ __global__ void __launch_bounds__(TX *TY)
     if constexpr (TT::TS) {
         __syncthreads();
         if (tid == 0) {
-            if (!failed && prev.lat >= 0) store_out(prev);
+            if (!failed && prev.lat >= 0) store_out(prev, prev_buf);
             bulk_wait_all();
         }
     }
