@@ -166,16 +166,21 @@ struct TmaTile {
     static constexpr int DESC_OFF = NS * STAGE;                // NSL x 128
     static constexpr int RHO_OFF = DESC_OFF + NSL * 128;       // 2 frames
     // The tile's post-collision output, [NPL][TY][TX] words, written by
-    // bulk tensor stores -- where it fits.  FP16 tiles keep two output
-    // tiles where they fit (ONE_BAR): the store of one tile is issued while
-    // the next is written, which leaves one block barrier per tile instead
-    // of two.
+    // bulk tensor stores (FP32 storage: one output tile where it fits, two
+    // block barriers per tile).  FP16 storage takes one block barrier per
+    // tile (ONE_BAR): tiles of up to 256 nodes store their nodes directly
+    // (coalesced 32-bit stores) and run three blocks per SM; larger tiles
+    // keep two output tiles, so that the store of one is issued while the
+    // next is written.
     static constexpr int OUT_BYTES = (NPL * NT * 4 + 127) / 128 * 128;
     static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
-    static constexpr bool TS = OUT_OFF + OUT_BYTES + 128 <= 232448;
-    static constexpr bool ONE_BAR =
-        S::kHalf && OUT_OFF + 2 * OUT_BYTES + 128 <= 232448;
-    static constexpr int NOUT = ONE_BAR ? 2 : (TS ? 1 : 0);
+    static constexpr bool ONE_BAR = S::kHalf;
+    static constexpr int NOUT =
+        S::kHalf ? (NT <= 256 ? 0 : (OUT_OFF + 2 * OUT_BYTES + 128 <= 232448 ? 2 : 0))
+                 : (OUT_OFF + OUT_BYTES + 128 <= 232448 ? 1 : 0);
+    static constexpr bool TS = NOUT > 0;
+    // blocks per SM the register budget is set for
+    static constexpr int MINB = S::kHalf && NT <= 256 ? 3 : 1;
     static constexpr int BAR_OFF = OUT_OFF + NOUT * OUT_BYTES;
     static constexpr int SMEM = BAR_OFF + 128;
     static_assert(SMEM <= 232448, "shared memory per block");
@@ -353,7 +358,7 @@ struct TmaMaps {
 };
 
 template <class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
     k_step_tma(StepArgs a, TmaMaps mp, const TileRec *__restrict__ sched,
                int nslots, int *__restrict__ err) {
     using TT = TmaTile<S, TX, TY>;
