@@ -196,15 +196,27 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return __ffma2_rn(a, b, c);
 }
 
+// c + h s for FP16 h and s, FP32 c: the product is exact, the sum rounded
+// once (the mixed-precision fused multiply-add of sm_100-family GPUs, so no
+// separate conversion of h is needed).
+__device__ __forceinline__ float fma_h(uint16_t h, uint16_t s, float c) {
+    float r;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(h), "h"(s), "f"(c));
+    return r;
+}
+constexpr uint16_t kH_InvDevScale = 0x1400;  // 2^-10 in FP16
+constexpr uint16_t kH_MinusOne = 0xBC00;     // -1 in FP16
+
 // The {A, B} values of one direction from their packed deviations and the
-// source's references {rho~_A, rho~_B}.
+// source's references {rho~_A, rho~_B}: rho~ + 2^-10 d, rounded once, as
+// dec16.
 __device__ __forceinline__ float2 dec_pair(uint32_t w, float2 ref) {
-    return fma2(__half22float2(bits_h2(w)), f2s(kInvDevScale), ref);
+    return make_float2(fma_h((uint16_t)(w & 0xFFFFu), kH_InvDevScale, ref.x),
+                       fma_h((uint16_t)(w >> 16), kH_InvDevScale, ref.y));
 }
 // Solute direction k from the word of its pair (k even: low half).
 __device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
-    const __half2 h = bits_h2(w);
-    return dec16(__half2float((k & 1) ? __high2half(h) : __low2half(h)), ref);
+    return fma_h((uint16_t)((k & 1) ? (w >> 16) : (w & 0xFFFFu)), kH_InvDevScale, ref);
 }
 
 // Encodes the scaled post-collision {A, B} values f[0..8] into the 8
@@ -216,9 +228,12 @@ __device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8]) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const float2 dv = fma2(f[i], f2s(kDevScale), n);
-        const __half2 h = __floats2half2_rn(dv.x, dv.y);
-        e = fma2(f2s(wq(i)), sub2(dv, __half22float2(h)), e);
-        w[i - 1] = h2_bits(h);
+        const uint32_t h = h2_bits(__floats2half2_rn(dv.x, dv.y));
+        // the quantisation errors dv - FP16(dv), exact
+        const float2 q = make_float2(fma_h((uint16_t)(h & 0xFFFFu), kH_MinusOne, dv.x),
+                                     fma_h((uint16_t)(h >> 16), kH_MinusOne, dv.y));
+        e = fma2(f2s(wq(i)), q, e);
+        w[i - 1] = h;
     }
     return fma2(e, f2s(kInvDevScale), f[0]);
 }
@@ -232,13 +247,14 @@ __device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
     float d[QS];
 #pragma unroll
     for (int k = 0; k < QS; ++k) d[k] = __fmaf_rn(gh[k], kDevScale, n);
-    const __half2 h01 = __floats2half2_rn(d[0], d[1]);
-    const __half2 h23 = __floats2half2_rn(d[2], d[3]);
-    const float2 b01 = __half22float2(h01), b23 = __half22float2(h23);
-    const float e = __fadd_rn(__fadd_rn(__fsub_rn(d[0], b01.x), __fsub_rn(d[1], b01.y)),
-                              __fadd_rn(__fsub_rn(d[2], b23.x), __fsub_rn(d[3], b23.y)));
-    w01 = h2_bits(h01);
-    w23 = h2_bits(h23);
+    w01 = h2_bits(__floats2half2_rn(d[0], d[1]));
+    w23 = h2_bits(__floats2half2_rn(d[2], d[3]));
+    // the quantisation errors d_k - FP16(d_k), exact
+    const float e = __fadd_rn(
+        __fadd_rn(fma_h((uint16_t)(w01 & 0xFFFFu), kH_MinusOne, d[0]),
+                  fma_h((uint16_t)(w01 >> 16), kH_MinusOne, d[1])),
+        __fadd_rn(fma_h((uint16_t)(w23 & 0xFFFFu), kH_MinusOne, d[2]),
+                  fma_h((uint16_t)(w23 >> 16), kH_MinusOne, d[3])));
     rc = __fmaf_rn(e, 0.25f * kInvDevScale, c);
 }
 

@@ -523,8 +523,15 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
         }
         // ring of the density frame: the lanes of the first warps take
         // RW consecutive ring cells each (consecutive addresses, no
-        // shared-memory bank conflicts)
+        // shared-memory bank conflicts).  FP16 storage: when the previous
+        // tile of this block is the one just above (a strip walks down a
+        // tile column), the top ring row is that tile's last frame row
+        // (its last row of nodes and their side ring cells, same step),
+        // copied instead of pulled again.
         {
+            const TileRec rp = s_rec[(k + NSL - 1) % NSL];
+            const bool above = S::kHalf && k > 0 && rp.lat == rc.lat &&
+                               rp.x0 == tx0 && rp.y0 + TY == ty0;
             const int r = warp * TT::RW + lane;
             if (lane < TT::RW && r < TT::NRING) {
                 int ry, rx;
@@ -535,7 +542,9 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
                 const int rmc = (ry + 1) * TT::MBX + rx - 1 + TT::MXO;
                 const int rpc = (ry + 1) * TT::BX + rx - 1 + TT::XO;
                 float2 q = make_float2(0.f, 0.f);
-                if (!(sm[rmc] & mb.force)) {
+                if (above && ry == 0) {
+                    q = reinterpret_cast<const float2 *>(srho((k + 1) & 1))[TY * TT::RX + rx];
+                } else if (!(sm[rmc] & mb.force)) {
                     // per lane: a warp-uniform choice here measured slower
                     const unsigned rbb = nb_bits<TT, -1>(sm, rmc, mb.pull);
                     q = sdens<S, TT>(tp, rpc, rbb, rbb == 0u);
