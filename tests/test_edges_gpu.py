@@ -27,6 +27,7 @@ FP16_TOL_SHORT = 5e-3
 # per-component relative bound (gpu_helpers.pop_rel_error; the reason is
 # given in test_parity_gpu.py)
 FP32_REL = 1e-4
+FP16_REL = 1.5e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,8 +55,9 @@ def test_full_sweep_sampled_capillaries(precision, tol):
         o.step(steps)
         np.testing.assert_array_equal(s.solid_mask(k), o.solid())
         assert pop_error(s.populations(k), oracle_pops(o)) < tol, k
-        if precision == "fp32":
-            assert_rel(s.populations(k), oracle_pops(o), FP32_REL)
+        rel = assert_rel(s.populations(k), oracle_pops(o),
+                         FP32_REL if precision == "fp32" else FP16_REL)
+        print("sweep sample %s lattice %d: %s" % (precision, k, rel))
     s.close()
 
 
@@ -74,8 +76,9 @@ def test_full_size_preform_both_storages():
             s.step(3)
             np.testing.assert_array_equal(s.solid_mask(), o.solid())
             assert pop_error(s.populations(), fo) < tol, precision
-            if precision == "fp32":
-                assert_rel(s.populations(), fo, FP32_REL)
+            rel = assert_rel(s.populations(), fo,
+                             FP32_REL if precision == "fp32" else FP16_REL)
+            print("full preform %s: %s" % (precision, rel))
 
 
 def _capillary(k_r, m_threshold, nx=96, ny=14):

@@ -216,16 +216,25 @@ def test_observables_match_oracle_definitions():
 
 # ---- FP16 storage -------------------------------------------------------
 #
-# Moving populations stored as FP16 deviations from w_i times the node's
-# own FP16-rounded reference, rest populations in FP32 carrying the
-# quantisation error, FP32 arithmetic.  Stated bounds (measured on the
-# small capillary: 4.9e-4 of w_i after 2000 steps, front within 1.2e-4 lu,
+# Populations stored as FP16 deviations of f_i / w_i from the node's FP32
+# reference (its rest population f_0 / w_0, which takes up the
+# quantisation error), FP32 arithmetic.  Stated bounds (measured on the
+# small capillary: 6.6e-4 of w_i after 2000 steps, front within 6e-4 lu,
 # mask and closure step exact; random non-equilibrium states, whose
-# deviations from w_i rho are up to ~0.5 rho: 1.1e-3 after 4 steps; the
+# deviations from w_i rho are up to ~0.5 rho: 1.8e-3 after one step; the
 # small preform over its run: below 3e-3):
 FP16_TOL_CAPILLARY = 1e-3
 FP16_TOL_LONG = 3e-3
 FP16_TOL_SHORT = 2e-3
+# per component, relative to the component's own density: the deviation
+# of a population from its node's reference is quantised to FP16's 11-bit
+# significand, so the bound follows the size of that deviation -- large at
+# interfaces, where the Shan-Chen shift is of order one, and in the random
+# non-equilibrium states (deviations up to half the density).  Measured:
+# random states 1.5e-2 after one step, small capillary 7.0e-3 after 2000
+# steps, small preform 5.9e-3, sweep sample 7.4e-3, closure case 2.2e-3.
+FP16_REL_RANDOM = 3e-2
+FP16_REL_LONG = 1.5e-2
 
 
 @pytest.mark.parametrize("nx,ny,seed", [(37, 23, 1), (130, 11, 5)])
@@ -249,6 +258,8 @@ def test_fp16_random_state_steps(nx, ny, seed):
         o.step(n)
         np.testing.assert_array_equal(s.solid_mask(), o.solid())
         assert pop_error(s.populations(), oracle_pops(o)) < FP16_TOL_SHORT
+        rel = assert_rel(s.populations(), oracle_pops(o), FP16_REL_RANDOM)
+        print("FP16 random state %dx%d after %d: %s" % (nx, ny, n, rel))
 
 
 def test_fp16_small_capillary_2000_steps():
@@ -265,7 +276,9 @@ def test_fp16_small_capillary_2000_steps():
         else:
             assert abs(go["front"] - oo["front"]) < 0.5
     err = pop_error(s.populations(), oracle_pops(o))
-    print("FP16 small capillary: max population error / w_i = %.3g" % err)
+    rel = assert_rel(s.populations(), oracle_pops(o), FP16_REL_LONG)
+    print("FP16 small capillary: max population error / w_i = %.3g, per "
+          "component %s" % (err, rel))
     assert err < FP16_TOL_CAPILLARY
     go = s.observables()[0]
     oo = A.lattice_observables(o)
@@ -341,6 +354,7 @@ def test_preform_small_fp32_and_fp16():
         assert pop_error(s32.populations(), fo) < FP32_TOL
         assert pop_error(s16.populations(), fo) < FP16_TOL_LONG
         assert_rel(s32.populations(), fo, FP32_REL)
+        print("FP16 preform 192:", assert_rel(s16.populations(), fo, FP16_REL_LONG))
     assert (o.solid() != geom.solid).sum() > 0
     g32 = s32.observables()[0]
     led = o.ledger()
