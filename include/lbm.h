@@ -147,10 +147,12 @@ enum {
 
 typedef struct lbm_handle lbm_handle;
 
-/* Creates a handle holding one lattice.  Copies the geometry to the device
- * (host->device once) and allocates everything the steps need; *out is
- * NULL on failure.  Returns EINVAL for bad sizes or parameters, ENOMEM,
- * ECUDA. */
+/* Creates a handle holding one lattice: the capillary or pore geometry and
+ * the model constants of paper Sec. II (both fluids start at rest,
+ * reading c13; the solute at the given concentration).  Copies the
+ * geometry to the device (host->device once) and allocates everything the
+ * steps need; *out is NULL on failure.  Returns EINVAL for bad sizes or
+ * parameters, ENOMEM, ECUDA. */
 lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p,
                       lbm_handle **out);
 
@@ -163,7 +165,10 @@ lbm_status lbm_create_batch(const lbm_geometry *g, const lbm_params *p,
  * own stream).  The caller keeps the stream alive while bound. */
 lbm_status lbm_set_stream(lbm_handle *h, void *cuda_stream);
 
-/* Advances every lattice by n >= 0 steps (asynchronous). */
+/* Advances every lattice by n >= 0 time steps of the paper's Sec. II
+ * update (collision with the Martys-Chen forces, streaming with half-way
+ * bounce-back, solute advection-diffusion, surface reaction, deposit and
+ * growth; readings c1-c12).  Asynchronous on the bound stream. */
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
 /* Number of completed steps. */
@@ -176,12 +181,15 @@ int32_t lbm_count(const lbm_handle *h);
  * LBM_ENAN (after filling out) if some lattice holds a non-finite value. */
 lbm_status lbm_observables(lbm_handle *h, lbm_obs *out);
 
-/* Current solid mask of lattice k: n must be ny*nx bytes. */
+/* Current solid mask of lattice k (the grown solid of paper Sec. II-III,
+ * 1 = solid): n must be ny*nx bytes, row-major.  Synchronizes. */
 lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k, uint8_t *host,
                               size_t n);
 
-/* Copies a field of lattice k (see LBM_FIELD_*) to host memory of exactly
- * `bytes` bytes.  Synchronizes. */
+/* Copies a field of lattice k (see LBM_FIELD_*; the post-streaming
+ * populations the Sec. II update is stated in, the deposit, the densities)
+ * to host memory of exactly `bytes` bytes.  Project addition for parity
+ * checks and analysis.  Synchronizes. */
 lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
                           void *host, size_t bytes);
 
@@ -192,7 +200,8 @@ lbm_status lbm_get_fields(lbm_handle *h, int32_t k, int32_t which,
 lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
                           const void *host, size_t bytes);
 
-/* Writes / reads the complete device state (populations in their stored
+/* Checkpoint and resume (project addition; the paper has no counterpart).
+ * Writes / reads the complete device state (populations in their stored
  * precision, mask, deposit, ledgers, counters, step) to / from a file; a
  * loaded handle continues bit for bit as the saved one would have.  The
  * handle given to lbm_load must have been created with the same
@@ -280,7 +289,7 @@ lbm_status lbm_plan_tiles(const int32_t *nx, const int32_t *ny, int32_t count,
  *
  * Allocates nothing (no cudaMalloc, no cudaFree, no allocating library
  * routine).  Its working memory is a file-scope device array of
- * LBM_STATIC_MAX_COLUMNS column records (about 1.8 MB) that every GPU
+ * LBM_STATIC_MAX_COLUMNS column records (about 1.44 MB) that every GPU
  * which loads this library holds until the process exits; nx above that
  * limit returns LBM_EINVAL.  The first call on a device looks up the
  * array's device address, with that device current; make that first call
@@ -288,8 +297,13 @@ lbm_status lbm_plan_tiles(const int32_t *nx, const int32_t *ny, int32_t count,
  * calls whose kernels overlap on the GPU (different streams, or different
  * host threads) race and must be serialized by the caller.  Each call
  * writes every record it reads, so no clearing is needed between calls.
+ * The result's nonfinite flag covers only the state passed in (a handle's
+ * lbm_observables also keeps a flag set by earlier steps, e.g. at a node
+ * that has since turned solid).
  * Returns LBM_EINVAL for NULL pointers or bad sizes, LBM_ECUDA if the
- * set-up or the launch fails. */
+ * set-up or the launch fails, or if a CUDA error was already pending when
+ * the call was made (nothing is launched then and the pending error is not
+ * cleared). */
 #define LBM_STATIC_MAX_COLUMNS 16384
 lbm_status lbm_observables_static(const float *pops, const uint8_t *solid,
                                   const uint8_t *solid0,

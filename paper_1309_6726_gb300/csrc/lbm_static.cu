@@ -252,6 +252,9 @@ extern "C" lbm_status lbm_observables_static(
     bk.ny = ny;
     bk.cap_x0 = cap_x0;
     bk.cap_x1 = cap_x1;
+    // an error left pending by earlier, unrelated work is not this call's:
+    // report it without launching (and without clearing it)
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
     k_static_columns<<<(nx + 127) / 128, 128, 0, s>>>(pops, solid, solid0,
                                                       deposit, nx, ny, cols);
     k_static_reduce<<<1, 256, 0, s>>>(cols, bk, out);
