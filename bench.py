@@ -229,7 +229,7 @@ def time_e2e(geoms, params, precision, steps, observe_every):
     """Whole job through the C ABI with host buffers: create (host->device
     copy of geometry and initial fields from pinned host memory), steps,
     observables read back every `observe_every` steps and at the end, final
-    solid masks read back."""
+    solid masks of every lattice read back (one call)."""
     import torch
     from paper_1309_6726_gb300 import lbm
     geoms = pinned(geoms)
@@ -244,8 +244,7 @@ def time_e2e(geoms, params, precision, steps, observe_every):
         done += k
         s.observables(allow_nan=True)
         n_obs += 1
-    for k in range(len(geoms)):
-        s.solid_mask(k)
+    s.solid_masks()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     s.close()

@@ -186,6 +186,12 @@ lbm_status lbm_observables(lbm_handle *h, lbm_obs *out);
 lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k, uint8_t *host,
                               size_t n);
 
+/* Current solid masks of every lattice of the handle, one call: each
+ * lattice's ny*nx bytes (row-major, 1 = solid) back to back in lattice
+ * order; n must be the sum of nx*ny.  Project addition (one device pass
+ * and one copy for a whole batch).  Synchronizes. */
+lbm_status lbm_get_solid_masks(lbm_handle *h, uint8_t *host, size_t n);
+
 /* Copies a field of lattice k (see LBM_FIELD_*; the post-streaming
  * populations the Sec. II update is stated in, the deposit, the densities)
  * to host memory of exactly `bytes` bytes.  Project addition for parity

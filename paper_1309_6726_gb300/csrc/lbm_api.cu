@@ -28,9 +28,6 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
 cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
 int tma_box_x(int tx);
 int tma_mask_box_x(int tx);
-__global__ void k_rest_state(const LatDesc *, int, const float *,
-                             const float *, const float *, const uint8_t *,
-                             float *);
 __global__ void k_unstream(const LatDesc *, int, const float *,
                            const uint8_t *, uint8_t, void *, bool);
 __global__ void k_export(const LatDesc *, int, const void *, const uint8_t *,
@@ -41,9 +38,17 @@ __global__ void k_settle(const LatDesc *, int, const void *, uint8_t *,
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
 __global__ void k_solid_mask(const LatDesc *, int, const uint8_t *, uint8_t,
                              uint8_t *);
-__global__ void k_mask_init(const LatDesc *, int, const uint8_t *, uint8_t *);
-__global__ void k_col_init(const LatDesc *, int, const uint8_t *, int32_t *,
-                           int16_t *, LatState *);
+__global__ void k_mask_init_all(const LatDesc *, int, const int64_t *,
+                                const int64_t *, const uint8_t *, uint8_t *);
+__global__ void k_col_init_all(const LatDesc *, int, const int64_t *,
+                               const int64_t *, const uint8_t *, int32_t *,
+                               int16_t *, LatState *);
+__global__ void k_init_rest_all(const LatDesc *, int, const int64_t *,
+                                const int64_t *, const float *, const uint8_t *,
+                                void *, bool);
+__global__ void k_solid_mask_all(const LatDesc *, int, const int64_t *,
+                                 const int64_t *, const uint8_t *, uint8_t,
+                                 uint8_t *);
 __global__ void k_obs_columns(const LatDesc *, const int32_t *,
                               const int64_t *, int, const void *,
                               const uint8_t *, const double *, long long,
@@ -67,6 +72,7 @@ struct lbm_handle {
     bool use_tma = true;
     std::vector<LatDesc> desc;
     std::vector<int64_t> col_base;   // first column of lattice l (all columns)
+    std::vector<int64_t> in_off_host;  // first node of lattice l, unpadded (count + 1)
     int64_t ncols = 0;               // columns of all lattices
     int64_t nsec = 0;                // section columns of all lattices
     int ntiles = 0;
@@ -77,6 +83,9 @@ struct lbm_handle {
     int32_t *d_tile_lat = nullptr;
     int32_t *d_col_lat = nullptr;
     int64_t *d_col_base = nullptr;
+    int64_t *d_in_off = nullptr;       // node then row prefixes, 2 (count + 1)
+    int64_t total_rows = 0;
+    uint8_t *d_masks = nullptr;        // all solid masks, unpadded (on first use)
     void *d_pop[2] = {nullptr, nullptr};
     uint8_t *d_mask = nullptr;
     double *d_m = nullptr;
@@ -135,6 +144,7 @@ static cudaError_t dalloc(T **p, size_t n) {
 
 static void free_all(lbm_handle *h) {
     void *ps[] = {h->d_desc, h->d_tile_lat, h->d_col_lat, h->d_col_base,
+                  h->d_in_off, h->d_masks,
                   h->d_pop[0], h->d_pop[1],
                   h->d_mask, h->d_m, h->d_col_fluid, h->d_wall0, h->d_st,
                   h->d_step, h->d_done, h->d_cols, h->d_obs, h->d_canon,
@@ -455,6 +465,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     // ---- packed ragged layout ------------------------------------------
     h->desc.resize(count);
     h->col_base.resize(count);
+    h->in_off_host.assign(count + 1, 0);
     int64_t pop = 0, node = 0, cols = 0, sec = 0;
     int tiles = 0;
     for (int l = 0; l < count; ++l) {
@@ -495,6 +506,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.index = l;
         d.pad_ = 0;
         h->max_nodes = std::max(h->max_nodes, (size_t)G.nx * G.ny);
+        h->in_off_host[l + 1] = h->in_off_host[l] + (int64_t)G.nx * G.ny;
     }
     h->ntiles = tiles;
     h->pop_elems = pop;
@@ -522,6 +534,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     AL(h->d_tile_lat, tiles);
     AL(h->d_col_lat, cols);
     AL(h->d_col_base, count);
+    AL(h->d_in_off, 2 * (count + 1));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[0], pop * esz);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pop[1], pop * esz);
     AL(h->d_mask, node);
@@ -555,6 +568,43 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     bad(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking), "stream");
     h->stream = h->own;
     cudaStream_t s = h->stream;
+    // Initial state of the whole batch: every lattice's inputs are copied
+    // into one device staging area (one copy per input array, issued back
+    // to back on the handle's stream, landing while the host builds the
+    // tensor maps and the schedule below), then one launch per set-up
+    // kernel covers all lattices.
+    const int64_t total = h->in_off_host.back();
+    float *rho3 = nullptr;
+    uint8_t *sol = nullptr;
+    // prefixes over the lattices (count + 1 entries each): nodes (staging
+    // offsets), rows, rows with the ghost band, section columns
+    const int C1 = count + 1;
+    int64_t *pre = nullptr;
+    if (st == LBM_OK) {
+        bad(dalloc(&rho3, 3 * (size_t)total), "alloc");
+        bad(dalloc(&sol, (size_t)total), "alloc");
+        bad(dalloc(&pre, 4 * (size_t)C1), "alloc");
+    }
+    std::vector<int64_t> pre_h(4 * C1, 0);
+    for (int l = 0; l < count; ++l) {
+        pre_h[l + 1] = h->in_off_host[l + 1];
+        pre_h[C1 + l + 1] = pre_h[C1 + l] + h->desc[l].ny;
+        pre_h[2 * C1 + l + 1] = pre_h[2 * C1 + l] + h->desc[l].ny + 2 * GHOST;
+        pre_h[3 * C1 + l] = h->desc[l].col_off;
+    }
+    pre_h[3 * C1 + count] = h->nsec;
+    h->total_rows = pre_h[C1 + count];
+    if (st == LBM_OK) {
+        bad(cudaMemcpyAsync(pre, pre_h.data(), pre_h.size() * 8, cudaMemcpyHostToDevice, s), "prefix");
+        bad(cudaMemcpyAsync(h->d_in_off, pre_h.data(), 2 * C1 * 8, cudaMemcpyHostToDevice, s), "prefix");
+    }
+    for (int l = 0; l < count && st == LBM_OK; ++l) {
+        const int64_t N = (int64_t)h->desc[l].nx * h->desc[l].ny, o = h->in_off_host[l];
+        bad(cudaMemcpyAsync(rho3 + 3 * o, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
+        bad(cudaMemcpyAsync(rho3 + 3 * o + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
+        bad(cudaMemcpyAsync(rho3 + 3 * o + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
+        bad(cudaMemcpyAsync(sol + o, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
+    }
     bad(cudaMemcpy(h->d_desc, h->desc.data(), count * sizeof(LatDesc), cudaMemcpyHostToDevice), "desc");
     bad(cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
     bad(cudaMemcpy(h->d_col_lat, col_lat.data(), cols * sizeof(int32_t), cudaMemcpyHostToDevice), "cols");
@@ -579,38 +629,24 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         }
     }
     bad(cudaMemset(h->d_done, 0, sizeof(unsigned)), "memset");
-    // initial rest state of every lattice through the unstream path
-    float *tmp = nullptr;
-    uint8_t *tsol = nullptr;
-    if (st == LBM_OK) {
-        bad(dalloc(&tmp, 3 * h->max_nodes), "alloc");
-        bad(dalloc(&tsol, h->max_nodes), "alloc");
-    }
     // the memsets above ran on the legacy stream; the handle's stream does
     // not wait for it
     if (st == LBM_OK) bad(cudaDeviceSynchronize(), "sync");
-    // one lattice at a time through the staging buffers; stream order keeps
-    // a lattice's copies behind the previous lattice's kernels
-    for (int l = 0; l < count && st == LBM_OK; ++l) {
-        const LatDesc &d = h->desc[l];
-        const size_t N = (size_t)d.nx * d.ny;
-        bad(cudaMemcpyAsync(tmp, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
-        bad(cudaMemcpyAsync(tmp + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
-        bad(cudaMemcpyAsync(tmp + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
-        bad(cudaMemcpyAsync(tsol, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
-        k_mask_init<<<dim3((d.nx + 2 * GHOST + 127) / 128, d.ny + 2 * GHOST), 128, 0, s>>>(
-            h->d_desc, l, tsol, h->d_mask);
-        if (d.cap_x1 > d.cap_x0)
-            k_col_init<<<(d.cap_x1 - d.cap_x0 + 127) / 128, 128, 0, s>>>(
-                h->d_desc, l, tsol, h->d_col_fluid, h->d_wall0, h->d_st);
-        dim3 grid((d.nx + 127) / 128, d.ny), blk(128);
-        k_rest_state<<<grid, blk, 0, s>>>(h->d_desc, l, tmp, tmp + N, tmp + 2 * N, tsol, h->d_canon);
-        k_unstream<<<grid, blk, 0, s>>>(h->d_desc, l, h->d_canon, h->d_mask, 1, h->d_pop[0], h->half);
+    if (st == LBM_OK) {
+        k_mask_init_all<<<(unsigned)pre_h[2 * C1 + count], 128, 0, s>>>(
+            h->d_desc, count, pre + 2 * C1, pre, sol, h->d_mask);
+        if (h->nsec > 0)
+            k_col_init_all<<<(unsigned)((h->nsec + 255) / 256), 256, 0, s>>>(
+                h->d_desc, count, pre + 3 * C1, pre, sol, h->d_col_fluid,
+                h->d_wall0, h->d_st);
+        k_init_rest_all<<<(unsigned)h->total_rows, 128, 0, s>>>(
+            h->d_desc, count, pre + C1, pre, rho3, h->d_mask, h->d_pop[0], h->half);
         bad(cudaGetLastError(), "init kernels");
     }
     bad(cudaStreamSynchronize(s), "init sync");
-    if (tmp) cudaFree(tmp);
-    if (tsol) cudaFree(tsol);
+    if (rho3) cudaFree(rho3);
+    if (sol) cudaFree(sol);
+    if (pre) cudaFree(pre);
     if (st != LBM_OK) {
         free_all(h);
         delete h;
@@ -783,6 +819,23 @@ extern "C" lbm_status lbm_get_solid_mask(lbm_handle *h, int32_t k,
         h->d_desc, k, h->d_mask, mb.force, tmp);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(host, tmp, n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_solid_masks(lbm_handle *h, uint8_t *host,
+                                          size_t n) {
+    if (!h || !host) return fail(h, LBM_EINVAL, "bad argument");
+    if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
+    const int64_t total = h->in_off_host.back();
+    if (n != (size_t)total) return fail(h, LBM_EINVAL, "size mismatch");
+    if (!h->d_masks) CK(h, dalloc(&h->d_masks, (size_t)total));
+    const MaskBits mb(h->steps);
+    k_solid_mask_all<<<(unsigned)h->total_rows, 128, 0, h->stream>>>(
+        h->d_desc, h->count, h->d_in_off + h->count + 1, h->d_in_off, h->d_mask,
+        mb.force, h->d_masks);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(host, h->d_masks, n, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }

@@ -78,32 +78,59 @@ __device__ __forceinline__ void store_node(void *fout, const LatDesc &d,
     store_words16(static_cast<uint32_t *>(fout) + d.pop_off + own, pl, wv);
 }
 
-// Mask bytes of lattice l over its ghost band (columns -2 .. nx + 1, rows
-// -2 .. ny + 1; every image is its periodic source node) from the row-major
-// solid array of the lattice: solid -> all three time bits set.
-__global__ void k_mask_init(const LatDesc *desc, int l, const uint8_t *solid,
-                            uint8_t *mask_all) {
-    const LatDesc d = desc[l];
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GHOST;
-    const int y = (int)blockIdx.y - GHOST;
-    if (x >= d.nx + GHOST) return;
-    const int xs = wrapg(x, d.nx), ys = wrapg(y, d.ny);
-    mask_all[d.node_off + (int64_t)y * d.pitch + x] =
-        solid[(int64_t)ys * d.nx + xs] ? 7 : 0;
+// ---- set-up of a whole batch, one launch per kernel ------------------------
+// The inputs of every lattice sit back to back in device staging: lattice
+// l's nodes from in_off[l] (row-major ny*nx), solid bytes in `solid`, the
+// densities and concentration in rho3 as [rho_A | rho_B | C] blocks of
+// 3 * nx * ny floats from 3 * in_off[l].  One block takes one row of one
+// lattice (rows of all lattices numbered through an exclusive prefix of
+// per-lattice row counts, count + 1 entries; the block finds its lattice by
+// a binary search) and its threads walk the row's columns.
+
+__device__ __forceinline__ int lattice_of(const int64_t *pre, int count,
+                                          int64_t g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
-// Per section column of lattice l: fluid nodes, and the initial wall
+// Mask bytes over every lattice's ghost band (columns -2 .. nx + 1, rows
+// -2 .. ny + 1; every image is its periodic source node): solid -> all
+// three time bits set.  grow: prefix of ny + 4 (rows with the band).
+__global__ void k_mask_init_all(const LatDesc *desc, int count,
+                                const int64_t *grow, const int64_t *in_off,
+                                const uint8_t *solid, uint8_t *mask_all) {
+    const int l = lattice_of(grow, count, blockIdx.x);
+    const LatDesc &d = desc[l];
+    const int y = (int)(blockIdx.x - grow[l]) - GHOST;
+    const int ys = wrapg(y, d.ny);
+    const uint8_t *srow = solid + in_off[l] + (int64_t)ys * d.nx;
+    uint8_t *mrow = mask_all + d.node_off + (int64_t)y * d.pitch;
+    for (int x = (int)threadIdx.x - GHOST; x < d.nx + GHOST; x += blockDim.x)
+        mrow[x] = srow[x >= 0 && x < d.nx ? x : wrapg(x, d.nx)] ? 7 : 0;
+}
+
+// Per section column of every lattice: fluid nodes, and the initial wall
 // thickness from below and from above (runs of solid from each edge); a
-// column solid from the start sets the lattice's closure step to 0.
-__global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
-                           int32_t *col_fluid, int16_t *wall0, LatState *st) {
-    const LatDesc d = desc[l];
-    const int x = d.cap_x0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= d.cap_x1) return;
+// column solid from the start sets its lattice's closure step to 0.
+// cpre: prefix of the section widths (the lattices' col_off).
+__global__ void k_col_init_all(const LatDesc *desc, int count,
+                               const int64_t *cpre, const int64_t *in_off,
+                               const uint8_t *solid, int32_t *col_fluid,
+                               int16_t *wall0, LatState *st) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= cpre[count]) return;
+    const int l = lattice_of(cpre, count, g);
+    const LatDesc &d = desc[l];
+    const int x = d.cap_x0 + (int)(g - cpre[l]);
+    const uint8_t *sl = solid + in_off[l];
     int fl = 0, b = 0, t = 0;
     bool below = true;
     for (int y = 0; y < d.ny; ++y) {
-        const bool sv = solid[(int64_t)y * d.nx + x] != 0;
+        const bool sv = sl[(int64_t)y * d.nx + x] != 0;
         fl += !sv;
         if (below && sv) ++b;
         if (!sv) below = false;
@@ -119,6 +146,61 @@ __global__ void k_col_init(const LatDesc *desc, int l, const uint8_t *solid,
     wall0[2 * k + 1] = (int16_t)min(t, 32767);
 }
 
+// Stored initial state of every lattice: each fluid node at rest
+// equilibrium, f_i = w_i rho, g_k = C / 4 (reading c13), written in the
+// pull scheme's stored form (the post-collision values that one pull turns
+// into that state: f*_i(x) = f_i(x + e_i), or f_opp i(x) where x + e_i is
+// solid).  The mask must be built (k_mask_init_all) first.  rows: prefix
+// of ny.
+__global__ void k_init_rest_all(const LatDesc *desc, int count,
+                                const int64_t *rows, const int64_t *in_off,
+                                const float *rho3, const uint8_t *mask_all,
+                                void *fout, bool half) {
+    const int l = lattice_of(rows, count, blockIdx.x);
+    const LatDesc &d = desc[l];
+    const int y = (int)(blockIdx.x - rows[l]);
+    const uint8_t *mask = mask_all + d.node_off;
+    const int64_t N = (int64_t)d.nx * d.ny;
+    const float *ra = rho3 + 3 * in_off[l], *rb = ra + N, *cc = ra + 2 * N;
+    for (int x = threadIdx.x; x < d.nx; x += blockDim.x) {
+        const int64_t own = (int64_t)y * d.pitch + x;
+        if (mask[own] & 1) continue;  // solid: never read
+        const int64_t r = (int64_t)y * d.nx + x;
+        int64_t src[Q], ssrc[QS];
+        for (int i = 0; i < Q; ++i) {
+            const int xd = wrap1(x + cx(i), d.nx), yd = wrap1(y + cy(i), d.ny);
+            const bool b = mask[(int64_t)yd * d.pitch + xd] & 1;
+            src[i] = b ? r : (int64_t)yd * d.nx + xd;
+        }
+        for (int k = 0; k < QS; ++k) ssrc[k] = src[k + 1];  // D2Q4 k = D2Q9 k + 1
+        if (half) {
+            // the scaled populations f_i / w_i of a node at rest are its
+            // density, 4 g_k its concentration: no weights to divide out
+            float2 f[Q];
+            float gv[QS];
+            for (int i = 0; i < Q; ++i) f[i] = make_float2(ra[src[i]], rb[src[i]]);
+            for (int k = 0; k < QS; ++k) gv[k] = cc[ssrc[k]];
+            uint32_t wv[NW16];
+            enc_node16(f, gv, wv);
+            uint32_t *out = static_cast<uint32_t *>(fout) + d.pop_off;
+            store_words16(out + own, (int)d.plane, wv);
+            for_ghosts(x, y, d.nx, d.ny, d.pitch, (int)own,
+                       [&](int off) { store_words16(out + off, (int)d.plane, wv); });
+        } else {
+            float v[NPOP];
+            for (int i = 0; i < Q; ++i) {
+                // opposite directions share a weight
+                v[i] = wq(i) * ra[src[i]];
+                v[Q + i] = wq(i) * rb[src[i]];
+            }
+            for (int k = 0; k < QS; ++k) v[2 * Q + k] = 0.25f * cc[ssrc[k]];
+            store_node(fout, d, half, own, v);
+            for_ghosts(x, y, d.nx, d.ny, d.pitch, (int)own,
+                       [&](int off) { store_node(fout, d, half, off, v); });
+        }
+    }
+}
+
 // Solid mask of lattice l at the current step (force bit), row-major
 // [ny][nx] bytes 0/1.
 __global__ void k_solid_mask(const LatDesc *desc, int l,
@@ -132,24 +214,20 @@ __global__ void k_solid_mask(const LatDesc *desc, int l,
         (mask_all[d.node_off + (int64_t)y * d.pitch + x] & force) ? 1 : 0;
 }
 
-// canonical layout of one lattice: [22][ny][nx] floats, no padding.
-__global__ void k_rest_state(const LatDesc *desc, int l, const float *rho_a,
-                             const float *rho_b, const float *conc,
-                             const uint8_t *solid, float *canon) {
-    const LatDesc d = desc[l];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= d.nx || y >= d.ny) return;
-    const int64_t n = (int64_t)y * d.nx + x;
-    const int64_t P = (int64_t)d.nx * d.ny;
-    const bool fl = solid[n] == 0;
-    const float ra = fl ? rho_a[n] : 0.f, rb = fl ? rho_b[n] : 0.f;
-    const float c = fl ? conc[n] : 0.f;
-    for (int i = 0; i < Q; ++i) {
-        canon[i * P + n] = wq(i) * ra;
-        canon[(Q + i) * P + n] = wq(i) * rb;
-    }
-    for (int k = 0; k < QS; ++k) canon[(2 * Q + k) * P + n] = 0.25f * c;
+// Solid masks of every lattice at the current step (force bit), each
+// row-major [ny][nx] bytes 0/1, back to back in lattice order (in_off: node
+// prefix, rows: row prefix).
+__global__ void k_solid_mask_all(const LatDesc *desc, int count,
+                                 const int64_t *rows, const int64_t *in_off,
+                                 const uint8_t *mask_all, uint8_t force,
+                                 uint8_t *out) {
+    const int l = lattice_of(rows, count, blockIdx.x);
+    const LatDesc &d = desc[l];
+    const int y = (int)(blockIdx.x - rows[l]);
+    const uint8_t *mrow = mask_all + d.node_off + (int64_t)y * d.pitch;
+    uint8_t *orow = out + in_off[l] + (int64_t)y * d.nx;
+    for (int x = threadIdx.x; x < d.nx; x += blockDim.x)
+        orow[x] = (mrow[x] & force) ? 1 : 0;
 }
 
 // Stored state from post-streaming fields (exact inverse of the pull).
@@ -283,7 +361,8 @@ struct ObsPart {
 };
 
 // Sum of the 22 stored values of a node (A, B, solute), as readers decode
-// them.
+// them (the values load_pop returns, summed in the same order; FP16
+// storage reads each packed word and each reference once).
 __device__ __forceinline__ void stored_sums(const void *fin,
                                             const LatDesc &d, bool half,
                                             int64_t own, float &sa, float &sb,
@@ -291,6 +370,24 @@ __device__ __forceinline__ void stored_sums(const void *fin,
     sa = 0.f;
     sb = 0.f;
     sc = 0.f;
+    if (half) {
+        const uint32_t *w = static_cast<const uint32_t *>(fin) + d.pop_off;
+        const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
+        const float2 r = make_float2(ref[own], ref[d.plane + own]);
+        sa = wq(0) * r.x;
+        sb = wq(0) * r.y;
+        for (int i = 1; i < Q; ++i) {
+            const float2 f = dec_pair(w[(i - 1) * d.plane + own], r);
+            sa += wq(i) * f.x;
+            sb += wq(i) * f.y;
+        }
+        const float rc = ref[2 * d.plane + own];
+        const uint32_t w01 = w[W16_SOL * d.plane + own];
+        const uint32_t w23 = w[(W16_SOL + 1) * d.plane + own];
+        for (int k = 0; k < QS; ++k)
+            sc += 0.25f * dec_sol16(k < 2 ? w01 : w23, k, rc);
+        return;
+    }
     for (int i = 0; i < Q; ++i) {
         sa += load_pop(fin, d, half, i, own);
         sb += load_pop(fin, d, half, Q + i, own);
@@ -348,10 +445,51 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
     }
     part[w][lane] = p;
     __syncthreads();
+    // the lowest and highest fluid rows of the column (every warp)
+    int lo = 0x7fffffff, hi = -1, hsum = 0;
+    for (int k = 0; k < OBS_ROWS; ++k) {
+        lo = min(lo, part[k][lane].lo);
+        hi = max(hi, part[k][lane].hi);
+        hsum += part[k][lane].h;
+    }
+    // rho_A - rho_B at the rows the observables read, one row per warp (in
+    // parallel): the lowest and highest fluid row (wetting phase at the
+    // walls) and the two centerline rows
+    __shared__ float sphi[4][32];
+    __shared__ int sfl[4][32];
+    static_assert(OBS_ROWS >= 4, "one warp per phase row");
+    int l = 0, ny = 0, x = 0;
+    const uint8_t *mask = nullptr;
+    LatDesc d;
+    if (c < ncols_total) {
+        l = col_lat[c];
+        d = desc[l];
+        x = (int)(c - col_base[l]);
+        mask = mask_all + d.node_off;
+        ny = d.ny;
+    }
+    if (w < 4 && c < ncols_total) {
+        const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
+        const int y = w == 0 ? lo : w == 1 ? hi : w == 2 ? yc0 : yc1;
+        // lo/hi rows only where the column has fluid; centerline rows only
+        // where fluid now
+        bool need = w < 2 ? hsum > 0
+                          : !(mask[(int64_t)y * d.pitch + x] & mb.force);
+        float ph = 0.f;
+        if (need) {
+            float v[NPOP];
+            pull_node(fin, mask, d, half, mb.pull, x, y, v);
+            float ra = 0.f, rb = 0.f;
+            for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+            ph = ra - rb;
+        }
+        sphi[w][lane] = ph;
+        sfl[w][lane] = need;
+    }
+    __syncthreads();
     if (w != 0 || c >= ncols_total) return;
     double st[3] = {0, 0, 0};
     ColObs o = {};
-    int lo = 0x7fffffff, hi = -1;
     for (int k = 0; k < OBS_ROWS; ++k) {  // fixed order
         const ObsPart &q = part[k][lane];
         for (int j = 0; j < 3; ++j) st[j] += q.stored[j];
@@ -362,8 +500,6 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
         o.mass_m += q.dep;
         o.h += q.h;
         o.nonfinite |= q.nonfin;
-        lo = min(lo, q.lo);
-        hi = max(hi, q.hi);
     }
     // fluid content: stored content of the nodes fluid in the last step,
     // less what the pending ones received (totals over a lattice are exact;
@@ -371,22 +507,6 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
     o.mass_a = st[0] - o.pend_a;
     o.mass_b = st[1] - o.pend_b;
     o.mass_c = st[2] - o.pend_c;
-    const int l = col_lat[c];
-    const LatDesc d = desc[l];
-    const int x = (int)(c - col_base[l]);
-    const uint8_t *mask = mask_all + d.node_off;
-    const int ny = d.ny;
-    float v[NPOP];
-    // rho_A - rho_B of fluid node (x, y), pulled
-    auto phi = [&](int y) {
-        pull_node(fin, mask, d, half, mb.pull, x, y, v);
-        float ra = 0.f, rb = 0.f;
-        for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
-        return ra - rb;
-    };
-    auto fluid_now = [&](int y) {
-        return !(mask[(int64_t)y * d.pitch + x] & mb.force);
-    };
     if (o.h == 0) {
         o.b = ny;
         o.t = ny;
@@ -396,12 +516,11 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
         // highest fluid row; the wetting phase is read at those rows
         o.b = lo;
         o.t = ny - 1 - hi;
-        o.wet_lo = phi(lo) > 0.f;
-        o.wet_hi = hi == lo ? o.wet_lo : phi(hi) > 0.f;
+        o.wet_lo = sphi[0][lane] > 0.f;
+        o.wet_hi = sphi[1][lane] > 0.f;
     }
-    const int yc0 = (ny - 1) / 2, yc1 = ny / 2;
-    if (fluid_now(yc0)) { o.phi0 = phi(yc0); o.fl0 = 1; }
-    if (fluid_now(yc1)) { o.phi1 = yc1 == yc0 ? o.phi0 : phi(yc1); o.fl1 = 1; }
+    if (sfl[2][lane]) { o.phi0 = sphi[2][lane]; o.fl0 = 1; }
+    if (sfl[3][lane]) { o.phi1 = sphi[3][lane]; o.fl1 = 1; }
     out[c] = o;
 }
 

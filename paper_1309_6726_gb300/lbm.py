@@ -22,7 +22,8 @@ NPOP = 22
 #: exported symbols (every entry point the header declares)
 SYMBOLS = ("lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_step",
            "lbm_step_count", "lbm_count", "lbm_observables",
-           "lbm_get_solid_mask", "lbm_get_fields", "lbm_set_fields",
+           "lbm_get_solid_mask", "lbm_get_solid_masks", "lbm_get_fields",
+           "lbm_set_fields",
            "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
            "lbm_fit_reff", "lbm_observables_static", "lbm_autotune",
            "lbm_get_tuning", "lbm_plan_tiles")
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_observables.argtypes = [vp, C.POINTER(Obs)]
     lib.lbm_get_solid_mask.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint8),
                                        C.c_size_t]
+    lib.lbm_get_solid_masks.argtypes = [vp, C.POINTER(C.c_uint8), C.c_size_t]
     lib.lbm_get_fields.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
     lib.lbm_set_fields.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
     lib.lbm_save.argtypes = [vp, C.c_char_p]
@@ -127,11 +129,16 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
+_PARAM_KEYS = ("tau_a", "tau_b", "tau_d", "g_coh", "g_ads", "k_r",
+               "m_threshold", "c_in", "body_force_x")
+
+
 def _params(p, precision: int) -> Params:
-    g = p if isinstance(p, dict) else p.as_dict()
-    return Params(g["tau_a"], g["tau_b"], g["tau_d"], g["g_coh"], g["g_ads"],
-                  g["k_r"], g["m_threshold"], g["c_in"], g["body_force_x"],
-                  int(g["inlet"]), int(precision))
+    if isinstance(p, dict):
+        vals = [p[k] for k in _PARAM_KEYS] + [int(p["inlet"])]
+    else:
+        vals = [getattr(p, k) for k in _PARAM_KEYS] + [int(p.inlet)]
+    return Params(*vals, int(precision))
 
 
 class Solver:
@@ -154,6 +161,7 @@ class Solver:
         self._keep = []
         G = (Geometry * len(geoms))()
         P = (Params * len(geoms))()
+        u8p, fp = C.POINTER(C.c_uint8), C.POINTER(C.c_float)
         self.shapes = []
         for k, (g, p) in enumerate(zip(geoms, params)):
             solid = np.ascontiguousarray(g.solid, dtype=np.uint8)
@@ -169,11 +177,10 @@ class Solver:
                     raise ValueError("lattice %d: %s has shape %s, solid %s"
                                      % (k, name, a.shape, solid.shape))
             self._keep += [solid, ra, rb, cc]
-            G[k] = Geometry(nx, ny, solid.ctypes.data_as(C.POINTER(C.c_uint8)),
-                            ra.ctypes.data_as(C.POINTER(C.c_float)),
-                            rb.ctypes.data_as(C.POINTER(C.c_float)),
-                            cc.ctypes.data_as(C.POINTER(C.c_float)),
-                            int(g.cap_x0), int(g.cap_x1))
+            G[k] = Geometry(nx, ny, C.cast(solid.ctypes.data, u8p),
+                            C.cast(ra.ctypes.data, fp), C.cast(rb.ctypes.data, fp),
+                            C.cast(cc.ctypes.data, fp), int(g.cap_x0),
+                            int(g.cap_x1))
             P[k] = _params(p, prec)
             self.shapes.append((ny, nx))
         h = C.c_void_p()
@@ -234,6 +241,18 @@ class Solver:
         out = np.zeros((ny, nx), np.uint8)
         self._check(self._lib.lbm_get_solid_mask(
             self._h, k, out.ctypes.data_as(C.POINTER(C.c_uint8)), out.size))
+        return out
+
+    def solid_masks(self) -> list[np.ndarray]:
+        """Solid masks of every lattice, read back in one call."""
+        sizes = [ny * nx for ny, nx in self.shapes]
+        buf = np.zeros(sum(sizes), np.uint8)
+        self._check(self._lib.lbm_get_solid_masks(
+            self._h, buf.ctypes.data_as(C.POINTER(C.c_uint8)), buf.size))
+        out, o = [], 0
+        for (ny, nx), n in zip(self.shapes, sizes):
+            out.append(buf[o:o + n].reshape(ny, nx))
+            o += n
         return out
 
     def populations(self, k: int = 0) -> np.ndarray:

@@ -103,8 +103,10 @@ def test_batch_closes_each_lattice_at_its_own_step(precision):
         for o in ors:
             o.step(chunk)
         obs = s.observables()
+        masks = s.solid_masks()  # all lattices in one call
         for k, o in enumerate(ors):
             np.testing.assert_array_equal(s.solid_mask(k), o.solid())
+            np.testing.assert_array_equal(masks[k], o.solid())
             assert obs[k]["closure_step"] == o.closure_step, (k, o.step_count)
     steps = [o.closure_step for o in ors]
     print("%s closure steps: %s" % (precision, steps))
