@@ -1,25 +1,27 @@
 """A learned surrogate of the batched reactive solver (not part of the paper).
 
-The network of lbm_mlp.h maps the four parameters of one capillary run --
+The network of lbm_mlp.h maps the parameters of one capillary run --
 width W, reaction rate k_r, adhesion strength g_ads, viscosity ratio
-tau_A / tau_B -- to its infiltration curve, the front position z at 64
-log-spaced times, and to its pore-closure time.  It is trained on
-trajectories that the batched lattice Boltzmann solver generates (all
-members of a training set advance together in one persistent launch per
-step), and the solver stays the reference its error is measured against on
-held-out parameters
-and the fallback for parameters outside the training domain.
+tau_A / tau_B, and the capillary length L -- to its infiltration curve,
+the front position z at 64 log-spaced times, and to its pore-closure time.
+It is trained on trajectories that the batched lattice Boltzmann solver
+generates (the members of a training set advance together in persistent
+launches, one per step), and the solver stays the reference its error is
+measured against on held-out parameters and the fallback for parameters
+outside the training domain.
 
-Capillary length, reservoirs and the horizon are fixed for a surrogate
-(the inputs exclude them): by default L = 1024 with the sweep's 64-column
-A reservoir and 32-column outlet band, a horizon of 20000 steps, and
-parameters drawn as in the batched sweep (W uniform over 16-128, k_r
-log-uniform on [1e-5, 1e-2], contact angle uniform on [20, 60] degrees
-mapped to g_ads by the calibrated table, tau_A / tau_B uniform on
-[0.6, 1.5]).
+Parameters are drawn as in the batched sweep (W uniform over 16-128, L
+uniform over 1024-4096, k_r log-uniform on [1e-5, 1e-2], contact angle
+uniform on [20, 60] degrees mapped to g_ads by the calibrated table,
+tau_A / tau_B uniform on [0.6, 1.5]) with the sweep's 64-column A
+reservoir and 32-column outlet band.  The sweep draws L, so L is the fifth
+input (Washburn's front speed scales as 1 / L, Eq. 1); a surrogate trained
+on one length (a length range of one value) sees that input as constant.
+The horizon is fixed for a surrogate.
 
     python -m paper_1309_6726_gb300.surrogate [--train 4096] [--held-out 256]
-        [--length 1024] [--steps 20000] [--ensemble 5] [--fit-steps 16000]
+        [--length-min 1024] [--length-max 4096] [--steps 40000]
+        [--ensemble 5] [--fit-steps 16000]
 
 prints one JSON line with the dataset cost, the fit and the errors against
 the solver.
@@ -44,6 +46,8 @@ W_RANGE = (16, 128)
 K_RANGE = (1e-5, 1e-2)
 THETA_RANGE = (20.0, 60.0)
 RATIO_RANGE = (0.6, 1.5)
+L_RANGE = (1024, 4096)
+N_IN = 5  # W, log10 k_r, g_ads, tau ratio, L
 
 
 def time_grid(t_max: int, n: int = N_TIMES, t_first: int = T_FIRST) -> np.ndarray:
@@ -63,8 +67,10 @@ def time_grid(t_max: int, n: int = N_TIMES, t_first: int = T_FIRST) -> np.ndarra
     return t
 
 
-def draw_members(count: int, seed: int, length: int = 1024):
-    """Run parameters drawn as in the batched sweep, capillary length fixed."""
+def draw_members(count: int, seed: int, length=L_RANGE):
+    """Run parameters drawn as in the batched sweep; `length` is a fixed
+    capillary length or a (min, max) range drawn uniformly over integers."""
+    lo, hi = (length, length) if isinstance(length, int) else length
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
@@ -72,7 +78,8 @@ def draw_members(count: int, seed: int, length: int = 1024):
         k = float(10 ** rng.uniform(math.log10(K_RANGE[0]), math.log10(K_RANGE[1])))
         th = float(rng.uniform(*THETA_RANGE))
         tr = float(rng.uniform(*RATIO_RANGE))
-        out.append(I.SweepMember(w, length, k, th, tr))
+        length_k = int(rng.integers(lo, hi + 1))
+        out.append(I.SweepMember(w, length_k, k, th, tr))
     return out
 
 
@@ -82,10 +89,16 @@ def _g_range():
     return min(a, b), max(a, b)
 
 
-def features(members) -> np.ndarray:
-    """Network inputs in [-1, 1]: W, log10 k_r, g_ads, tau ratio."""
+def _l_range(length):
+    return (length, length) if isinstance(length, int) else tuple(length)
+
+
+def features(members, length=L_RANGE) -> np.ndarray:
+    """Network inputs in [-1, 1]: W, log10 k_r, g_ads, tau ratio and L over
+    the length range (0 when the range is a single length)."""
     g0, g1 = _g_range()
     lk0, lk1 = math.log10(K_RANGE[0]), math.log10(K_RANGE[1])
+    l0, l1 = _l_range(length)
     rows = []
     for m in members:
         g = I.g_ads_for_angle(m.theta_deg)
@@ -94,39 +107,49 @@ def features(members) -> np.ndarray:
             2 * (math.log10(m.k_r) - lk0) / (lk1 - lk0) - 1,
             2 * (g - g0) / (g1 - g0) - 1,
             2 * (m.tau_ratio - RATIO_RANGE[0]) / (RATIO_RANGE[1] - RATIO_RANGE[0]) - 1,
+            0.0 if l1 == l0 else 2 * (m.length - l0) / (l1 - l0) - 1,
         ])
     return np.asarray(rows, np.float32)
 
 
-def in_domain(members, length: int) -> np.ndarray:
-    """True where a run's parameters lie inside the training domain."""
-    f = features(members)
-    ok = np.all(np.abs(f) <= 1.0 + 1e-6, axis=1)
-    return ok & np.array([m.length == length for m in members])
+def in_domain(members, length=L_RANGE) -> np.ndarray:
+    """True where a run's parameters lie inside the training domain (the
+    parameter box and the length range)."""
+    l0, l1 = _l_range(length)
+    f = features(members, length)
+    ok = np.all(np.abs(f[:, :4]) <= 1.0 + 1e-6, axis=1)
+    return ok & np.array([l0 <= m.length <= l1 for m in members])
 
 
-def run_trajectories(members, t_grid, precision: str = "fp32"):
-    """Advances all members together on the GPU and records the front
-    position at each time of t_grid and the closure step (-1: none)."""
+def run_trajectories(members, t_grid, precision: str = "fp32",
+                     chunk: int = 1024):
+    """Advances the members on the GPU, `chunk` of them together in one
+    batch, and records the front position at each time of t_grid and the
+    closure step (-1: none)."""
     import torch
     from . import lbm
-    pairs = [I.sweep_lattice(m) for m in members]
+    z = np.full((len(members), len(t_grid)), np.nan)
+    closure = np.full(len(members), -1, np.int64)
+    bad = np.zeros(len(members), bool)
+    nodes = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = lbm.Solver([g for g, _ in pairs], [p for _, p in pairs], precision)
-    z = np.full((len(members), len(t_grid)), np.nan)
-    done = 0
-    for j, t in enumerate(t_grid):
-        s.step(int(t) - done)
-        done = int(t)
-        obs = s.observables(allow_nan=True)
-        z[:, j] = [o["front"] for o in obs]
-    closure = np.array([o["closure_step"] for o in obs], np.int64)
-    bad = np.array([bool(o["nonfinite"]) for o in obs])
+    for c0 in range(0, len(members), chunk):
+        part = members[c0:c0 + chunk]
+        pairs = [I.sweep_lattice(m) for m in part]
+        s = lbm.Solver([g for g, _ in pairs], [p for _, p in pairs], precision)
+        done = 0
+        for j, t in enumerate(t_grid):
+            s.step(int(t) - done)
+            done = int(t)
+            obs = s.observables(allow_nan=True)
+            z[c0:c0 + len(part), j] = [o["front"] for o in obs]
+        closure[c0:c0 + len(part)] = [o["closure_step"] for o in obs]
+        bad[c0:c0 + len(part)] = [bool(o["nonfinite"]) for o in obs]
+        nodes += sum(int((g.solid == 0).sum()) for g, _ in pairs)
+        s.close()
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
-    nodes = sum(int((g.solid == 0).sum()) for g, _ in pairs)
-    s.close()
     z[bad] = np.nan
     return {"z": z, "closure": closure, "nonfinite": bad, "seconds": seconds,
             "fluid_nodes": nodes, "steps": int(t_grid[-1])}
@@ -200,7 +223,7 @@ class FitLog:
 
 
 class Surrogate:
-    """An ensemble of networks (4 inputs, 3 x 256 tanh, 65 outputs) on the
+    """An ensemble of networks (5 inputs, 3 x 256 tanh, 65 outputs) on the
     GPU, each from its own initialisation and minibatch order; the
     prediction is their mean."""
 
@@ -209,10 +232,10 @@ class Surrogate:
         from . import mlp
         self.nets = []
         for k in range(members):
-            net = mlp.Mlp(4, hidden, layers, N_TIMES + 1, max_batch)
+            net = mlp.Mlp(N_IN, hidden, layers, N_TIMES + 1, max_batch)
             rng = np.random.default_rng([seed, k])
             ws, bs = [], []
-            for r, c in mlp.layer_shapes(4, hidden, layers, N_TIMES + 1):
+            for r, c in mlp.layer_shapes(N_IN, hidden, layers, N_TIMES + 1):
                 lim = math.sqrt(6.0 / (r + c))  # Glorot uniform
                 ws.append(rng.uniform(-lim, lim, (r, c)))
                 bs.append(np.zeros(r))
@@ -273,15 +296,17 @@ class Surrogate:
             net.close()
 
 
-def predict_or_solve(model: Surrogate, members, t_grid, length: int):
-    """Answers from the network inside the training domain and from the
-    solver (the fallback) outside it; returns (front, closure, source)."""
+def predict_or_solve(model: Surrogate, members, t_grid, length=L_RANGE):
+    """Answers from the network inside the training domain (parameter box
+    and length range) and from the solver (the fallback) outside it;
+    returns (front, closure, source)."""
     t_max = int(t_grid[-1])
     inside = in_domain(members, length)
     z = np.full((len(members), len(t_grid)), np.nan)
     c = np.full(len(members), -1, np.int64)
     if inside.any():
-        zi, ci = decode(model.predict(features([m for m, o in zip(members, inside) if o])), t_max)
+        zi, ci = decode(model.predict(features(
+            [m for m, o in zip(members, inside) if o], length)), t_max)
         z[inside], c[inside] = zi, ci
     if (~inside).any():
         r = run_trajectories([m for m, o in zip(members, inside) if not o], t_grid)
@@ -293,8 +318,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=4096)
     ap.add_argument("--held-out", type=int, default=256)
-    ap.add_argument("--length", type=int, default=1024)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--length-min", type=int, default=L_RANGE[0])
+    ap.add_argument("--length-max", type=int, default=L_RANGE[1])
+    ap.add_argument("--steps", type=int, default=40000)
     ap.add_argument("--fit-steps", type=int, default=16000,
                     help="Adam steps per ensemble member")
     ap.add_argument("--batch", type=int, default=1024)
@@ -312,8 +338,9 @@ def main(argv=None):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     grid = time_grid(args.steps)
-    train_m = draw_members(args.train, args.seed, args.length)
-    test_m = draw_members(args.held_out, args.seed + 1, args.length)
+    lr = (args.length_min, args.length_max)
+    train_m = draw_members(args.train, args.seed, lr)
+    test_m = draw_members(args.held_out, args.seed + 1, lr)
     if args.data:
         dd = np.load(args.data)
         tr = {"z": dd["z_train"], "closure": dd["c_train"],
@@ -322,20 +349,20 @@ def main(argv=None):
         te = {"z": dd["z_test"], "closure": dd["c_test"],
               "nonfinite": np.all(np.isnan(dd["z_test"]), axis=1),
               "seconds": float("nan"), "fluid_nodes": 0, "steps": args.steps}
-        if not (np.array_equal(dd["x_train"], features(train_m)) and
+        if not (np.array_equal(dd["x_train"], features(train_m, lr)) and
                 np.array_equal(dd["times"], grid)):
             raise SystemExit("--data was written for other parameters")
     else:
         tr = run_trajectories(train_m, grid)
         te = run_trajectories(test_m, grid)
-    x, y = features(train_m), targets(tr["z"], tr["closure"], args.steps)
+    x, y = features(train_m, lr), targets(tr["z"], tr["closure"], args.steps)
     if args.save_data:
         np.savez(args.save_data, x_train=x, z_train=tr["z"],
-                 c_train=tr["closure"], x_test=features(test_m),
+                 c_train=tr["closure"], x_test=features(test_m, lr),
                  z_test=te["z"], c_test=te["closure"], times=grid)
     model = Surrogate(seed=args.seed, members=args.ensemble)
     log = model.fit(x, y, steps=args.fit_steps, batch=args.batch)
-    xt = features(test_m)
+    xt = features(test_m, lr)
     model.predict(xt)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -346,7 +373,7 @@ def main(argv=None):
     if args.save:
         np.save(args.save, np.stack(model.params()))
     out = {
-        "length": args.length, "steps": args.steps, "times": len(grid),
+        "length_range": list(lr), "steps": args.steps, "times": len(grid),
         "train_runs": args.train, "held_out_runs": args.held_out,
         "train_nonfinite": int(tr["nonfinite"].sum()),
         "held_out_nonfinite": int(te["nonfinite"].sum()),

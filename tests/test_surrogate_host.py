@@ -49,15 +49,24 @@ def test_targets_round_trip_and_missing_runs():
 def test_features_span_the_training_domain():
     members = S.draw_members(400, seed=3)
     f = S.features(members)
-    assert f.shape == (400, 4) and f.dtype == np.float32
+    assert f.shape == (400, S.N_IN) and f.dtype == np.float32
     assert np.all(np.abs(f) <= 1.0 + 1e-6)
+    # lengths drawn over the sweep's range, as the sweep draws them
+    lengths = np.array([m.length for m in members])
+    assert lengths.min() >= S.L_RANGE[0] and lengths.max() <= S.L_RANGE[1]
+    assert lengths.max() - lengths.min() > 0.8 * (S.L_RANGE[1] - S.L_RANGE[0])
     # the corners of the ranges map to -1 and +1
-    lo = I.SweepMember(S.W_RANGE[0], 1024, S.K_RANGE[0], S.THETA_RANGE[1],
-                       S.RATIO_RANGE[0])
-    hi = I.SweepMember(S.W_RANGE[1], 1024, S.K_RANGE[1], S.THETA_RANGE[0],
-                       S.RATIO_RANGE[1])
+    lo = I.SweepMember(S.W_RANGE[0], S.L_RANGE[0], S.K_RANGE[0],
+                       S.THETA_RANGE[1], S.RATIO_RANGE[0])
+    hi = I.SweepMember(S.W_RANGE[1], S.L_RANGE[1], S.K_RANGE[1],
+                       S.THETA_RANGE[0], S.RATIO_RANGE[1])
     np.testing.assert_allclose(S.features([lo, hi]),
-                               [[-1, -1, -1, -1], [1, 1, 1, 1]], atol=1e-6)
+                               [[-1, -1, -1, -1, -1], [1, 1, 1, 1, 1]],
+                               atol=1e-6)
+    # a single training length: that input is constant (0)
+    fixed = S.draw_members(10, seed=4, length=1024)
+    assert {m.length for m in fixed} == {1024}
+    assert np.all(S.features(fixed, 1024)[:, 4] == 0.0)
 
 
 def test_in_domain_excludes_other_lengths_and_ranges():
@@ -65,8 +74,12 @@ def test_in_domain_excludes_other_lengths_and_ranges():
     wide = I.SweepMember(200, 1024, 1e-3, 30.0, 1.0)
     fast = I.SweepMember(64, 1024, 5e-2, 30.0, 1.0)
     longer = I.SweepMember(64, 2048, 1e-3, 30.0, 1.0)
-    assert S.in_domain([ok, wide, fast, longer], 1024).tolist() == [
-        True, False, False, False]
+    too_long = I.SweepMember(64, 5000, 1e-3, 30.0, 1.0)
+    runs = [ok, wide, fast, longer, too_long]
+    assert S.in_domain(runs, 1024).tolist() == [
+        True, False, False, False, False]
+    assert S.in_domain(runs, (1024, 4096)).tolist() == [
+        True, False, False, True, False]
 
 
 def test_compare_to_solver_by_hand():
