@@ -41,10 +41,11 @@ METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated err
 #: 22 x 2 B x 2 + 1 = 89.  The roofline's `achieved` uses these.
 BYTES_PER_NODE = {"fp32": 177.0, "fp16": 89.0}
 #: bytes the layout actually stores and reloads per fluid-node update
-#: (reported beside the algorithmic count): FP16 storage keeps 13 32-bit
-#: words per node (8 half2 A/B deviation pairs, 2 half2 solute pairs, 3
-#: FP32 references), read and written: 104 B, + 1 mask byte.
-STORED_BYTES_PER_NODE = {"fp32": 177.0, "fp16": 105.0}
+#: (reported beside the algorithmic count): FP16 storage keeps 15 32-bit
+#: words per node (8 half2 A/B deviation pairs, 2 half2 solute pairs, 2
+#: half2 linear-reference pairs, 3 FP32 references), read and written:
+#: 120 B, + 1 mask byte.
+STORED_BYTES_PER_NODE = {"fp32": 177.0, "fp16": 121.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel

@@ -64,13 +64,20 @@ typedef enum {
 typedef enum {
     LBM_FP32 = 0, /* populations stored as FP32 */
     LBM_FP16 = 1  /* populations stored as FP16 deviations from per-node
-                     FP32 references: f_i / w_i - rho~ per component (rho~
-                     = f_0 / w_0, the rest population, stored in FP32) and
-                     4 g_k - C~ for the solute, scaled by 2^10, the A and B
-                     deviations of a direction packed in one 32-bit word;
-                     the references take up the rounding of the deviations,
-                     so each node keeps its mass to FP32 rounding.  13
-                     32-bit words per node against FP32's 22. */
+                     references exact in FP32: per component, direction i
+                     reads back f_i / w_i = rho~ + e_i . v + 2^-10 d_i, with
+                     rho~ = f_0 / w_0 (the rest population, FP32) and v,
+                     for the component with the larger rest population
+                     and where |v_x| + |v_y| <= rho~, the odd part of the
+                     axis populations ((f^_1 - f^_3) / 2, (f^_2 - f^_4) /
+                     2, rounded to FP16; else 0), so the majority's FP16
+                     d_i holds only the second-order and non-equilibrium
+                     part;
+                     the solute reads back 4 g_k = C~ + 2^-10 d_k.  The A and
+                     B values of a direction share one 32-bit word; the
+                     references take up the rounding of the deviations, so
+                     each node keeps its mass to FP32 rounding.  15 32-bit
+                     words per node against FP32's 22. */
 } lbm_precision;
 
 /* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,

@@ -929,7 +929,7 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
 
 // ---- checkpoints -----------------------------------------------------------
 
-static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '4'};
+static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '5'};
 
 struct CkptHeader {
     char magic[8];

@@ -23,8 +23,11 @@ __device__ __forceinline__ float load_pop(const void *base, const LatDesc &d,
         const int comp = q < Q ? 0 : 1, i = q - comp * Q;
         const float r = ref[comp * d.plane + e];
         if (i == 0) return wq(0) * r;
-        const float2 dv = __half22float2(bits_h2(w[(i - 1) * d.plane + e]));
-        return wq(i) * dec16(comp ? dv.y : dv.x, r);
+        const int sh = comp ? 16 : 0;  // B in the high halves
+        const float ri = ref_dir(i, false, r, (uint16_t)(w[W16_VEL * d.plane + e] >> sh),
+                                 (uint16_t)(w[(W16_VEL + 1) * d.plane + e] >> sh));
+        return wq(i) * fma_h((uint16_t)(w[(i - 1) * d.plane + e] >> sh),
+                             kH_InvDevScale, ri);
     }
     const int k = q - 2 * Q;
     return 0.25f * dec_sol16(w[(W16_SOL + (k >> 1)) * d.plane + e], k,
@@ -376,8 +379,10 @@ __device__ __forceinline__ void stored_sums(const void *fin,
         const float2 r = make_float2(ref[own], ref[d.plane + own]);
         sa = wq(0) * r.x;
         sb = wq(0) * r.y;
+        const uint32_t wx = w[W16_VEL * d.plane + own];
+        const uint32_t wy = w[(W16_VEL + 1) * d.plane + own];
         for (int i = 1; i < Q; ++i) {
-            const float2 f = dec_pair(w[(i - 1) * d.plane + own], r);
+            const float2 f = dec_pair(i, false, w[(i - 1) * d.plane + own], r, wx, wy);
             sa += wq(i) * f.x;
             sb += wq(i) * f.y;
         }

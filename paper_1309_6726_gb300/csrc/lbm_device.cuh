@@ -7,9 +7,10 @@
 //     `pitch` (a multiple of 32 words, so every row starts on a 128-byte
 //     boundary):
 //       FP32 storage: 22 planes (A: 9, B: 9, solute: 4);
-//       FP16 storage: 13 planes (see the codec below): 8 planes of half2
+//       FP16 storage: 15 planes (see the codec below): 8 planes of half2
 //       deviation pairs {A_i, B_i} of the moving populations, 2 planes of
-//       half2 solute deviation pairs, and 3 FP32 reference planes
+//       half2 solute deviation pairs, 2 planes of half2 linear-reference
+//       pairs {v_A, v_B} (x, then y) and 3 FP32 reference planes
 //       (rho~_A, rho~_B, C~);
 //   every plane (populations, mask) has a two-node ghost band around the
 //     lattice -- rows -2, -1, ny, ny + 1 and columns -2, -1, nx, nx + 1 --
@@ -34,10 +35,11 @@ namespace lbmk {
 constexpr int Q = 9;      // D2Q9 per fluid component
 constexpr int QS = 4;     // D2Q4 solute
 constexpr int NPOP = 22;  // FP32 storage: 9 + 9 + 4 planes per lattice
-// FP16 storage: 13 planes of 32-bit words per lattice (see the codec)
-constexpr int NW16 = 13;
+// FP16 storage: 15 planes of 32-bit words per lattice (see the codec)
+constexpr int NW16 = 15;
 constexpr int W16_SOL = 8;   // half2 {C_0, C_1}, then {C_2, C_3}
-constexpr int W16_REF = 10;  // FP32 rho~_A, rho~_B, C~
+constexpr int W16_VEL = 10;  // half2 {v_A, v_B} along x, then along y
+constexpr int W16_REF = 12;  // FP32 rho~_A, rho~_B, C~
 
 // D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
 __host__ __device__ __forceinline__ constexpr int cx(int i) {
@@ -144,26 +146,57 @@ constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 // FP16 storage keeps, per node, the populations in scaled form -- f^_i =
 // f_i / w_i for the D2Q9 components (the equilibrium is then
 // rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u) with no weight) and g^_k = 4 g_k
-// for the solute -- as FP16 deviations from a per-node FP32 reference:
-//   A, B:   reference rho~ (the rest population f^_0 itself), moving
-//           i = 1..8 as d_i = 2^10 (f^_i - rho~) in FP16, the A and B
-//           deviations of one direction packed in one half2 word;
-//           read back f^_i = rho~ + 2^-10 d_i (one fused multiply-add);
+// for the solute -- as FP16 deviations from a per-node reference that is
+// exact in FP32:
+//   A, B:   the reference of direction i is linear in e_i,
+//             r_i = rho~ + e_i . v,
+//           rho~ the rest population f^_0 (FP32) and, for the component
+//           with the larger rest population at the node, v = ((f^_1 -
+//           f^_3) / 2, (f^_2 - f^_4) / 2) rounded to FP16 (the odd part of
+//           the axis populations, 3 rho u at equilibrium) where |v_x| +
+//           |v_y| <= f^_0, else v = 0 (and v = 0 for the minority phase);
+//           the moving i = 1..8 are
+//           stored as d_i = 2^10 (f^_i - r_i) in FP16, the A and B values
+//           of one direction (deviations, and v per axis) packed in one
+//           half2 word; read back f^_i = r_i + 2^-10 d_i;
 //   solute: reference C~ (the concentration), d_k = 2^10 (g^_k - C~), two
 //           directions per half2 word; g^_k = C~ + 2^-10 d_k.
-// The deviation carries only the velocity and non-equilibrium parts, so
-// FP16's 11-bit significand applies to a quantity 10-100x smaller than
-// f^_i; the reference is FP32 and local, so the minority component (rho ~
-// 0.006) keeps the majority's relative accuracy.  The power-of-two scale
-// keeps small deviations out of FP16's subnormal range.
+// The fluid deviation is then only the even second-order part 9/2 rho
+// (e.u)^2 - 3/2 rho u.u plus the non-equilibrium part, so FP16's 11-bit
+// significand applies to a quantity about u times smaller than with the
+// rest population alone as reference: in a slow bulk flow (u ~ 1e-3) the
+// read-back is as accurate as an FP32 value.  With the rest population
+// alone the rounding of the 3 rho e.u part (relative 2^-11 of it, at every
+// node and step) slowed a 4096 x 128 capillary's imbibition by a few
+// percent against FP32 and the FP64 solution; with the linear reference
+// the front agrees with FP32 to 0.01 lattice units after 15000 steps.
+// At equilibrium the deviation of direction i is 3 rho s + 9/2 rho s^2
+// (s = e_i.u) against the rest population and 9/2 rho s^2 against r_i,
+// which is no larger for every i exactly when |s| <= 1/3 for every i,
+// i.e. |u_x| + |u_y| <= 1/3 or |v_x| + |v_y| <= rho: the writer takes v
+// only there (against f^_0 <= rho, so a little inside it).  Beyond it,
+// at strongly forced nodes, the linear reference would enlarge the
+// deviation of the directions whose linear and quadratic parts have
+// opposite signs.  The minority phase keeps the rest population alone as
+// well: with v there, the worst per-component error of minority
+// populations next to walls (rho ~ 1e-3, large force shifts) grew to 2.6
+// times that of the rest-only reference over 40 steps of a small preform
+// against the FP64 solution.  The reader does not need to know which was
+// chosen: v = 0 reads back as the rest-only reference.
+// Since v is rounded to FP16 before either side uses it, writer and reader
+// form the same r_i (the mixed fused multiply-adds below; x term first);
+// v's own rounding only moves part of the deviation into d.  The
+// power-of-two scale keeps small deviations out of FP16's subnormal range.
 //
 // Mass: the writer quantises every deviation, then adds the exact
 // quantisation error sum_i w_i 2^-10 (d_i - FP16(d_i)) (each term exact in
-// FP32, the sum small) to the stored reference.  Since the reference enters
-// all nine read-backs with weights summing to one, the stored content of
-// the node equals its FP32 post-collision content up to one rounding at the
-// reference's magnitude, and the shift moves no momentum (sum_i w_i e_i =
-// 0).  The solute does the same with weights 1/4.  Readers round every
+// FP32, the sum small) to the stored reference.  Since rho~ enters all
+// nine read-backs with weights summing to one, and the linear terms cancel
+// in the weighted sum (sum_i w_i e_i = 0; each r_i is rounded once per
+// axis, and is exact when v's last bit is no finer than rho~'s), the
+// stored content of the node equals its FP32 post-collision content up to
+// roundings at the reference's magnitude, and the shift moves no momentum.
+// The solute does the same with weights 1/4.  Readers round every
 // read-back exactly as written here (explicit fused multiply-adds), so
 // all code paths rebuild the same FP32 values from the same bits.
 constexpr float kDevScale = 1024.0f;
@@ -172,14 +205,9 @@ constexpr float kInvDevScale = 1.0f / 1024.0f;
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
-__device__ __forceinline__ __half2 bits_h2(uint32_t w) {
-    return *reinterpret_cast<__half2 *>(&w);
-}
+__device__ __forceinline__ uint16_t lo16(uint32_t w) { return (uint16_t)(w & 0xFFFFu); }
+__device__ __forceinline__ uint16_t hi16(uint32_t w) { return (uint16_t)(w >> 16); }
 
-// Read-back of one scaled value from its FP16 deviation and reference.
-__device__ __forceinline__ float dec16(float d, float ref) {
-    return __fmaf_rn(d, kInvDevScale, ref);
-}
 // ---- packed FP32 pairs ------------------------------------------------------
 // The FP16 path carries the two fluid components side by side as
 // {A, B} float2 values and does their (identical) arithmetic with the
@@ -205,33 +233,63 @@ __device__ __forceinline__ float fma_h(uint16_t h, uint16_t s, float c) {
     return r;
 }
 constexpr uint16_t kH_InvDevScale = 0x1400;  // 2^-10 in FP16
+constexpr uint16_t kH_One = 0x3C00;          // 1 in FP16
 constexpr uint16_t kH_MinusOne = 0xBC00;     // -1 in FP16
 
-// The {A, B} values of one direction from their packed deviations and the
-// source's references {rho~_A, rho~_B}: rho~ + 2^-10 d, rounded once, as
-// dec16.
-__device__ __forceinline__ float2 dec_pair(uint32_t w, float2 ref) {
-    return make_float2(fma_h((uint16_t)(w & 0xFFFFu), kH_InvDevScale, ref.x),
-                       fma_h((uint16_t)(w >> 16), kH_InvDevScale, ref.y));
+// Reference r_i = rho~ + e_i . v of direction i (1..8) for one component,
+// v's FP16 bits vx, vy: one mixed fused multiply-add per nonzero component
+// of e_i, x first.  flip: the direction opp(i) instead (e = -e_i; the
+// bounced-back value of a pull, a select when i is a constant).
+__device__ __forceinline__ float ref_dir(int i, bool flip, float rho,
+                                         uint16_t vx, uint16_t vy) {
+    float r = rho;
+    if (cx(i) != 0) r = fma_h(vx, (cx(i) > 0) != flip ? kH_One : kH_MinusOne, r);
+    if (cy(i) != 0) r = fma_h(vy, (cy(i) > 0) != flip ? kH_One : kH_MinusOne, r);
+    return r;
+}
+
+// The {A, B} values of direction i (opp(i) if flip) from their packed
+// deviations w, the source's references {rho~_A, rho~_B} and its
+// linear-reference words wx, wy (a word the direction does not use is not
+// read): r_i + 2^-10 d, rounded as the writer rounds.
+__device__ __forceinline__ float2 dec_pair(int i, bool flip, uint32_t w,
+                                           float2 ref, uint32_t wx,
+                                           uint32_t wy) {
+    return make_float2(
+        fma_h(lo16(w), kH_InvDevScale, ref_dir(i, flip, ref.x, lo16(wx), lo16(wy))),
+        fma_h(hi16(w), kH_InvDevScale, ref_dir(i, flip, ref.y, hi16(wx), hi16(wy))));
 }
 // Solute direction k from the word of its pair (k even: low half).
 __device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
-    return fma_h((uint16_t)((k & 1) ? (w >> 16) : (w & 0xFFFFu)), kH_InvDevScale, ref);
+    return fma_h((k & 1) ? hi16(w) : lo16(w), kH_InvDevScale, ref);
 }
 
 // Encodes the scaled post-collision {A, B} values f[0..8] into the 8
-// direction words w[0..7] and the references {rho~_A, rho~_B} (mass-exact,
-// see above).
-__device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8]) {
-    const float2 n = mul2(f2s(-kDevScale), f[0]);
+// direction words w[0..7], the linear-reference words wv[0..1] (x, y) and
+// the references {rho~_A, rho~_B} (mass-exact, see above).
+__device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8],
+                                         uint32_t wv[2]) {
+    // v for the component with the larger rest population (the majority
+    // phase at the node) where |v_x| + |v_y| <= f^_0, 0 otherwise (see
+    // above)
+    const float2 vx = mul2(f2s(0.5f), sub2(f[1], f[3]));
+    const float2 vy = mul2(f2s(0.5f), sub2(f[2], f[4]));
+    const bool ua = f[0].x >= f[0].y && fabsf(vx.x) + fabsf(vy.x) <= f[0].x;
+    const bool ub = f[0].y >= f[0].x && fabsf(vx.y) + fabsf(vy.y) <= f[0].y;
+    wv[0] = h2_bits(__floats2half2_rn(ua ? vx.x : 0.f, ub ? vx.y : 0.f));
+    wv[1] = h2_bits(__floats2half2_rn(ua ? vy.x : 0.f, ub ? vy.y : 0.f));
     float2 e = f2s(0.f);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const float2 dv = fma2(f[i], f2s(kDevScale), n);
+        const float2 r = make_float2(ref_dir(i, false, f[0].x, lo16(wv[0]), lo16(wv[1])),
+                                     ref_dir(i, false, f[0].y, hi16(wv[0]), hi16(wv[1])));
+        // f^_i - r_i is exact where the two are within a factor of two
+        // (everywhere the deviation is small), the scale exact
+        const float2 dv = mul2(sub2(f[i], r), f2s(kDevScale));
         const uint32_t h = h2_bits(__floats2half2_rn(dv.x, dv.y));
         // the quantisation errors dv - FP16(dv), exact
-        const float2 q = make_float2(fma_h((uint16_t)(h & 0xFFFFu), kH_MinusOne, dv.x),
-                                     fma_h((uint16_t)(h >> 16), kH_MinusOne, dv.y));
+        const float2 q = make_float2(fma_h(lo16(h), kH_MinusOne, dv.x),
+                                     fma_h(hi16(h), kH_MinusOne, dv.y));
         e = fma2(f2s(wq(i)), q, e);
         w[i - 1] = h;
     }
@@ -251,19 +309,20 @@ __device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
     w23 = h2_bits(__floats2half2_rn(d[2], d[3]));
     // the quantisation errors d_k - FP16(d_k), exact
     const float e = __fadd_rn(
-        __fadd_rn(fma_h((uint16_t)(w01 & 0xFFFFu), kH_MinusOne, d[0]),
-                  fma_h((uint16_t)(w01 >> 16), kH_MinusOne, d[1])),
-        __fadd_rn(fma_h((uint16_t)(w23 & 0xFFFFu), kH_MinusOne, d[2]),
-                  fma_h((uint16_t)(w23 >> 16), kH_MinusOne, d[3])));
+        __fadd_rn(fma_h(lo16(w01), kH_MinusOne, d[0]),
+                  fma_h(hi16(w01), kH_MinusOne, d[1])),
+        __fadd_rn(fma_h(lo16(w23), kH_MinusOne, d[2]),
+                  fma_h(hi16(w23), kH_MinusOne, d[3])));
     rc = __fmaf_rn(e, 0.25f * kInvDevScale, c);
 }
 
-// The 13 stored words of a node from its scaled post-collision values, in
-// plane order (8 direction pairs, 2 solute pairs, rho~_A, rho~_B, C~).
+// The 15 stored words of a node from its scaled post-collision values, in
+// plane order (8 direction pairs, 2 solute pairs, 2 linear-reference
+// pairs, rho~_A, rho~_B, C~).
 __device__ __forceinline__ void enc_node16(const float2 f[Q], const float gh[QS],
                                            uint32_t v[NW16]) {
     float rc;
-    const float2 r = enc_ab(f, v);
+    const float2 r = enc_ab(f, v, v + W16_VEL);
     enc_sol(gh, v[W16_SOL], v[W16_SOL + 1], rc);
     v[W16_REF] = __float_as_uint(r.x);
     v[W16_REF + 1] = __float_as_uint(r.y);

@@ -15,8 +15,9 @@ namespace lbmk {
 //
 // Store32: plain FP32 planes, collision in the populations themselves.
 //
-// Store16: FP16 deviations from per-node FP32 references, A and B of one
-// direction packed in one half2 word (enc_node16 / dec_pair in
+// Store16: FP16 deviations from per-node references (FP32 rest population
+// plus an FP16 linear term), A and B of one direction packed in one half2
+// word (enc_node16 / dec_pair in
 // lbm_device.cuh); the collision works on the scaled populations f_i / w_i
 // and 4 g_k (fluid_update16).
 // ---------------------------------------------------------------------------
@@ -94,7 +95,7 @@ __device__ __forceinline__ void store22_f32(float *__restrict__ p, int plane,
     for (int k = 0; k < QS; ++k) p[(2 * Q + k) * plane] = g[k];
 }
 
-// FP16 storage: the 13 words of a node at p[w * plane].
+// FP16 storage: the 15 words of a node at p[w * plane].
 __device__ __forceinline__ void store_words16(uint32_t *__restrict__ p,
                                               int plane,
                                               const uint32_t v[NW16]) {
@@ -302,7 +303,7 @@ __device__ __forceinline__ float2 rcp2_guard(float2 x, float lim) {
 //   nb: densities {rho_A, rho_B} at x + e_i (index 1..8; 0 if solid);
 //   snb, ns: as for fluid_update.
 // The forces and the shift are those of forces_shift (readings c1, c3, c4),
-// formed for both components at once.  put(words) writes the node's 13
+// formed for both components at once.  put(words) writes the node's 15
 // stored words; its periodic images in the ghost band are written here.
 // Returns true if the node reached the threshold in this step.
 template <class Put>

@@ -100,8 +100,11 @@ __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
         const bool b = (bb >> i) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
         const int qi = b ? opp(i) : i;
-        f[i] = dec_pair(__ldg(w + (qi - 1) * d.plane + src),
-                        make_float2(__ldg(ref + src), __ldg(ref + d.plane + src)));
+        const uint32_t wx = cx(i) != 0 ? __ldg(w + W16_VEL * d.plane + src) : 0u;
+        const uint32_t wy = cy(i) != 0 ? __ldg(w + (W16_VEL + 1) * d.plane + src) : 0u;
+        f[i] = dec_pair(i, b, __ldg(w + (qi - 1) * d.plane + src),
+                        make_float2(__ldg(ref + src), __ldg(ref + d.plane + src)),
+                        wx, wy);
     }
 }
 

@@ -6,7 +6,7 @@
 //     walks the tiles of every lattice of the batch;
 //   * for each tile of TX x TY nodes, one thread issues a 3-D bulk tensor
 //     copy (cp.async.bulk.tensor) of the population planes (32-bit words:
-//     22 FP32 values, or the 13 words of FP16 storage) over the tile plus
+//     22 FP32 values, or the 15 words of FP16 storage) over the tile plus
 //     a halo of 2 rows and 4 columns -- the x start stays 16-byte aligned
 //     -- into shared memory, completing on an mbarrier; the mask box and
 //     the lattice descriptor come with it;
@@ -145,7 +145,7 @@ struct TmaTile {
     static constexpr int PL = BX * BY;            // words per plane
     static constexpr int MXO = 16;                // mask box: 16-byte aligned
     static constexpr int MBX = TX + 2 * MXO;
-    // population planes of a stage: 22 FP32, or the 13 words of FP16 storage
+    // population planes of a stage: 22 FP32, or the 15 words of FP16 storage
     static constexpr int NPL = S::kPlanes;
     static constexpr int POP_BYTES = NPL * PL * 4;
     static constexpr int MASK_BYTES = (MBX * BY + 127) / 128 * 128;
@@ -222,8 +222,9 @@ __device__ __forceinline__ void spull4(const float *tile, int c, unsigned bb4,
 }
 
 // FP16 storage: the scaled {A, B} populations pulled into the node at
-// stage cell c -- one packed word and the source's two FP32 references per
-// direction; the rest populations are the node's own references.
+// stage cell c -- per direction one packed deviation word, the source's two
+// FP32 references and its one or two linear-reference words; the rest
+// populations are the node's own references.
 template <class TT, bool BB>
 __device__ __forceinline__ void spull16ab(const uint32_t *tile, int c,
                                           unsigned bb, float2 f[Q]) {
@@ -234,8 +235,10 @@ __device__ __forceinline__ void spull16ab(const uint32_t *tile, int c,
         const bool b = BB && ((bb >> i) & 1u);
         const int cell = b ? c : c - cy(i) * TT::BX - cx(i);
         const int qi = b ? opp(i) : i;
-        f[i] = dec_pair(tile[(qi - 1) * TT::PL + cell],
-                        make_float2(ref[cell], ref[TT::PL + cell]));
+        const uint32_t wx = cx(i) != 0 ? tile[W16_VEL * TT::PL + cell] : 0u;
+        const uint32_t wy = cy(i) != 0 ? tile[(W16_VEL + 1) * TT::PL + cell] : 0u;
+        f[i] = dec_pair(i, b, tile[(qi - 1) * TT::PL + cell],
+                        make_float2(ref[cell], ref[TT::PL + cell]), wx, wy);
     }
 }
 
