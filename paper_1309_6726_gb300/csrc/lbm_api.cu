@@ -38,6 +38,8 @@ __global__ void k_settle(const LatDesc *, int, const void *, uint8_t *,
 __global__ void k_mask_agree(const LatDesc *, int, uint8_t *, long long);
 __global__ void k_solid_mask(const LatDesc *, int, const uint8_t *, uint8_t,
                              uint8_t *);
+__global__ void k_gather_inputs(const InPtrs *, int, const int64_t *, float *,
+                                uint8_t *);
 __global__ void k_mask_init_all(const LatDesc *, int, const int64_t *,
                                 const int64_t *, const uint8_t *, uint8_t *);
 __global__ void k_col_init_all(const LatDesc *, int, const int64_t *,
@@ -185,10 +187,37 @@ static bool valid_params(const lbm_params &p, std::string &why) {
     return true;
 }
 
+// The address under which this device reads a caller's array, or null if
+// it cannot (pageable host memory, another device's memory): pinned or
+// registered host memory is mapped into the device's address space (its
+// device pointer), managed memory and this device's memory are used as
+// they are.
+static const void *device_view(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    switch (a.type) {
+    case cudaMemoryTypeHost:
+        return a.devicePointer;
+    case cudaMemoryTypeDevice:
+        return a.device == dev ? a.devicePointer : nullptr;
+    case cudaMemoryTypeManaged:
+        return a.devicePointer ? a.devicePointer : p;
+    default:
+        return nullptr;
+    }
+}
+
 static void pick_tile(lbm_handle *h) {
     // measured fastest on the batched sweep: 64 x 8 for FP32 storage (one
-    // 512-thread block per SM), 64 x 4 for FP16 (its smaller tiles fit two
-    // 256-thread blocks per SM, which hides the issue-bound codec better)
+    // 512-thread block per SM), 64 x 4 for FP16 (two 256-thread blocks per
+    // SM hide the issue-bound codec better; also fastest on the single
+    // capillary and the preform)
     h->tx = 64;
     h->ty = h->half ? 4 : 8;
     const char *e = getenv("LBM_TILE");
@@ -568,11 +597,13 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     bad(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking), "stream");
     h->stream = h->own;
     cudaStream_t s = h->stream;
-    // Initial state of the whole batch: every lattice's inputs are copied
-    // into one device staging area (one copy per input array, issued back
-    // to back on the handle's stream, landing while the host builds the
-    // tensor maps and the schedule below), then one launch per set-up
-    // kernel covers all lattices.
+    // Initial state of the whole batch: every lattice's inputs go into one
+    // device staging area -- read in place by one gather kernel where the
+    // device can address the caller's arrays (pinned or registered host
+    // memory, device or managed memory), else copied by the host (one copy
+    // per pageable array) -- issued on the handle's stream and landing
+    // while the host builds the tensor maps and the schedule below; then
+    // one launch per set-up kernel covers all lattices.
     const int64_t total = h->in_off_host.back();
     float *rho3 = nullptr;
     uint8_t *sol = nullptr;
@@ -598,12 +629,40 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         bad(cudaMemcpyAsync(pre, pre_h.data(), pre_h.size() * 8, cudaMemcpyHostToDevice, s), "prefix");
         bad(cudaMemcpyAsync(h->d_in_off, pre_h.data(), 2 * C1 * 8, cudaMemcpyHostToDevice, s), "prefix");
     }
-    for (int l = 0; l < count && st == LBM_OK; ++l) {
-        const int64_t N = (int64_t)h->desc[l].nx * h->desc[l].ny, o = h->in_off_host[l];
-        bad(cudaMemcpyAsync(rho3 + 3 * o, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
-        bad(cudaMemcpyAsync(rho3 + 3 * o + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
-        bad(cudaMemcpyAsync(rho3 + 3 * o + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
-        bad(cudaMemcpyAsync(sol + o, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
+    InPtrs *d_ptrs = nullptr;
+    if (st == LBM_OK) {
+        std::vector<InPtrs> ptrs(count);
+        bool any = false;
+        for (int l = 0; l < count && st == LBM_OK; ++l) {
+            const int64_t N = (int64_t)h->desc[l].nx * h->desc[l].ny, o = h->in_off_host[l];
+            InPtrs &q = ptrs[l];
+            q.rho_a = static_cast<const float *>(device_view(g[l].rho_a));
+            q.rho_b = static_cast<const float *>(device_view(g[l].rho_b));
+            q.conc = static_cast<const float *>(device_view(g[l].conc));
+            q.solid = static_cast<const uint8_t *>(device_view(g[l].solid));
+            any = any || q.rho_a || q.rho_b || q.conc || q.solid;
+            if (!q.rho_a)
+                bad(cudaMemcpyAsync(rho3 + 3 * o, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
+            if (!q.rho_b)
+                bad(cudaMemcpyAsync(rho3 + 3 * o + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
+            if (!q.conc)
+                bad(cudaMemcpyAsync(rho3 + 3 * o + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
+            if (!q.solid)
+                bad(cudaMemcpyAsync(sol + o, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
+        }
+        if (any && st == LBM_OK) {
+            bad(dalloc(&d_ptrs, (size_t)count), "alloc");
+            if (st == LBM_OK)
+                bad(cudaMemcpyAsync(d_ptrs, ptrs.data(), count * sizeof(InPtrs),
+                                    cudaMemcpyHostToDevice, s), "pointers");
+            // at most 65535 lattices per launch (grid y)
+            for (int l0 = 0; l0 < count && st == LBM_OK; l0 += 65535) {
+                const unsigned ny_ = (unsigned)std::min(count - l0, 65535);
+                k_gather_inputs<<<dim3(16, ny_), 256, 0, s>>>(d_ptrs, l0, h->d_in_off,
+                                                              rho3, sol);
+                bad(cudaGetLastError(), "gather");
+            }
+        }
     }
     bad(cudaMemcpy(h->d_desc, h->desc.data(), count * sizeof(LatDesc), cudaMemcpyHostToDevice), "desc");
     bad(cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
@@ -647,6 +706,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     if (rho3) cudaFree(rho3);
     if (sol) cudaFree(sol);
     if (pre) cudaFree(pre);
+    if (d_ptrs) cudaFree(d_ptrs);
     if (st != LBM_OK) {
         free_all(h);
         delete h;

@@ -100,6 +100,27 @@ __device__ __forceinline__ int lattice_of(const int64_t *pre, int count,
     return lo;
 }
 
+// Gathers the inputs of lattices [l0, l0 + gridDim.y) into the device
+// staging area in one launch, reading the caller's arrays where the device
+// can address them (blockIdx.y: the lattice; the blocks in x stride over
+// its nodes): rho3 holds [rho_a | rho_b | conc] from 3 * in_off[l], sol the
+// solid bytes from in_off[l].  Entries left null were copied by the host.
+__global__ void k_gather_inputs(const InPtrs *ptr, int l0,
+                                const int64_t *in_off, float *rho3,
+                                uint8_t *sol) {
+    const int l = l0 + (int)blockIdx.y;
+    const InPtrs p = ptr[l];
+    const int64_t o = in_off[l], n = in_off[l + 1] - o;
+    float *r = rho3 + 3 * o;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (p.rho_a) r[k] = p.rho_a[k];
+        if (p.rho_b) r[n + k] = p.rho_b[k];
+        if (p.conc) r[2 * n + k] = p.conc[k];
+        if (p.solid) sol[o + k] = p.solid[k];
+    }
+}
+
 // Mask bytes over every lattice's ghost band (columns -2 .. nx + 1, rows
 // -2 .. ny + 1; every image is its periodic source node): solid -> all
 // three time bits set.  grow: prefix of ny + 4 (rows with the band).

@@ -139,6 +139,15 @@ struct StepArgs {
     int32_t stall_tx;
 };
 
+// One lattice's input arrays (row-major ny * nx) as the device addresses
+// them: pinned or registered host memory (mapped into the device's address
+// space), managed or this device's memory.  A null entry: the host copied
+// that array into the staging area instead (pageable host memory).
+struct InPtrs {
+    const float *rho_a, *rho_b, *conc;
+    const uint8_t *solid;
+};
+
 constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
