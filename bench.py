@@ -54,7 +54,7 @@ DEPOSIT_BYTES = 16.0
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.52, "fp16": None}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.61, "fp16": 126.32}
 
 
 def load_peaks():
