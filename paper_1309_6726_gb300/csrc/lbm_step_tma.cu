@@ -169,10 +169,11 @@ struct TmaTile {
     // bulk tensor stores (FP32 storage: one output tile where it fits, two
     // block barriers per tile).  FP16 storage takes one block barrier per
     // tile (ONE_BAR): tiles of up to 256 nodes store their nodes directly
-    // (coalesced 32-bit stores) and run two blocks per SM (128 registers:
-    // three blocks at 80 registers spilled and measured 10 % slower on the
-    // batched sweep at 64 x 4); larger tiles keep two output tiles, so
-    // that the store of one is issued while the next is written.
+    // (coalesced 32-bit stores) and run two blocks per SM (128 registers;
+    // the budget of three, 80 registers, spilled and measured 10 % slower
+    // on the batched sweep at 64 x 4, whose stages leave room for two
+    // blocks only); larger tiles keep two output tiles, so that the store
+    // of one is issued while the next is written.
     static constexpr int OUT_BYTES = (NPL * NT * 4 + 127) / 128 * 128;
     static constexpr int OUT_OFF = RHO_OFF + 2 * RHO_AL;
     static constexpr bool ONE_BAR = S::kHalf;

@@ -179,18 +179,25 @@ def test_checkpoint_continues_bit_for_bit(tmp_path, precision):
     np.testing.assert_array_equal(a.solid_mask(), b.solid_mask())
 
 
-def test_paper_scale_capillary_full_size():
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_paper_scale_capillary_full_size(precision):
     # The paper-scale configuration at its full size (4096 x 128) in the
     # launch configuration the benchmark times, for a stretch the oracle
     # finishes in seconds, compared element by element.
     geom, mp, _ = I.config_paper_scale(k_r=1e-3)
     mp.m_threshold = 0.004  # growth inside the short stretch
-    s, o = _pair(geom, mp)
+    s, o = _pair(geom, mp, precision)
     s.step(12)
     o.step(12)
     np.testing.assert_array_equal(s.solid_mask(), o.solid())
-    assert pop_error(s.populations(), oracle_pops(o)) < FP32_TOL
-    assert_rel(s.populations(), oracle_pops(o), FP32_REL)
+    fg, fo = s.populations(), oracle_pops(o)
+    if precision == "fp32":
+        assert pop_error(fg, fo) < FP32_TOL
+        assert_rel(fg, fo, FP32_REL)
+    else:
+        assert pop_error(fg, fo) < FP16_TOL_SHORT
+        print("FP16 paper scale, 12 steps: %.3g of w_i, %s"
+              % (pop_error(fg, fo), assert_rel(fg, fo, FP16_REL_LONG)))
     assert (o.solid() != geom.solid).sum() > 0
 
 
