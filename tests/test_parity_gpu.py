@@ -295,11 +295,14 @@ def test_fp16_small_capillary_2000_steps():
     oo = A.lattice_observables(o)
     assert go["closure_step"] == o.closure_step
     # mass of A (fluid + ledger): the rest populations carry the FP16
-    # quantisation, so only FP32 rounding remains; FP32 storage itself
-    # moves this total by about -1e-6 over these 2000 steps (the collision's
-    # sums round in FP32), hence twice that
+    # quantisation, so only FP32 rounding remains (measured -6.2e-7; FP32
+    # storage itself moves this total by about -1e-6 over these 2000 steps,
+    # the collision's sums rounding in FP32)
     ma = go["mass_a"] + go["ledger_a"]
-    assert ma == pytest.approx(oo["mass_a"] + oo["ledger_a"], rel=2e-6)
+    mo = oo["mass_a"] + oo["ledger_a"]
+    print("FP16 small capillary: A mass (fluid + ledger) relative error %.3g"
+          % (ma / mo - 1.0))
+    assert ma == pytest.approx(mo, rel=1e-6)
     for key in ("r_min", "r_ave", "r_h", "delta_e", "closed"):
         assert go[key] == pytest.approx(oo[key], abs=1e-9), key
 
