@@ -641,14 +641,16 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
             q.conc = static_cast<const float *>(device_view(g[l].conc));
             q.solid = static_cast<const uint8_t *>(device_view(g[l].solid));
             any = any || q.rho_a || q.rho_b || q.conc || q.solid;
+            // (the copy direction is inferred: pageable host memory, or
+            // another device's memory)
             if (!q.rho_a)
-                bad(cudaMemcpyAsync(rho3 + 3 * o, g[l].rho_a, N * 4, cudaMemcpyHostToDevice, s), "rho_a");
+                bad(cudaMemcpyAsync(rho3 + 3 * o, g[l].rho_a, N * 4, cudaMemcpyDefault, s), "rho_a");
             if (!q.rho_b)
-                bad(cudaMemcpyAsync(rho3 + 3 * o + N, g[l].rho_b, N * 4, cudaMemcpyHostToDevice, s), "rho_b");
+                bad(cudaMemcpyAsync(rho3 + 3 * o + N, g[l].rho_b, N * 4, cudaMemcpyDefault, s), "rho_b");
             if (!q.conc)
-                bad(cudaMemcpyAsync(rho3 + 3 * o + 2 * N, g[l].conc, N * 4, cudaMemcpyHostToDevice, s), "conc");
+                bad(cudaMemcpyAsync(rho3 + 3 * o + 2 * N, g[l].conc, N * 4, cudaMemcpyDefault, s), "conc");
             if (!q.solid)
-                bad(cudaMemcpyAsync(sol + o, g[l].solid, N, cudaMemcpyHostToDevice, s), "solid");
+                bad(cudaMemcpyAsync(sol + o, g[l].solid, N, cudaMemcpyDefault, s), "solid");
         }
         if (any && st == LBM_OK) {
             bad(dalloc(&d_ptrs, (size_t)count), "alloc");
