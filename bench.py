@@ -39,13 +39,13 @@ METRIC = "reactive 2-comp LB GLUPS & % HBM roofline, mixed vs FP32 at stated err
 #: D2Q9, 4 D2Q4) read once and written once at the storage precision, the
 #: mask byte read once -- FP32: 22 x 4 B x 2 + 1 = 177; 16-bit storage:
 #: 22 x 2 B x 2 + 1 = 89.  The roofline's `achieved` uses these.
-BYTES_PER_NODE = {"fp32": 177.0, "fp16": 89.0}
+BYTES_PER_NODE = {"fp32": 177.0, "fp16": 89.0, "bf16": 89.0}
 #: bytes the layout actually stores and reloads per fluid-node update
 #: (reported beside the algorithmic count): FP16 storage keeps 15 32-bit
 #: words per node (8 half2 A/B deviation pairs, 2 half2 solute pairs, 2
 #: half2 linear-reference pairs, 3 FP32 references), read and written:
 #: 120 B, + 1 mask byte.
-STORED_BYTES_PER_NODE = {"fp32": 177.0, "fp16": 121.0}
+STORED_BYTES_PER_NODE = {"fp32": 177.0, "fp16": 121.0, "bf16": 121.0}
 #: deposit read + write (FP64) at reacting (surface) nodes, per such node
 DEPOSIT_BYTES = 16.0
 #: DRAM bytes read + written per fluid-node update by the step kernel
@@ -54,7 +54,7 @@ DEPOSIT_BYTES = 16.0
 #: 512-capillary state is too large to capture; traffic scales with the
 #: fluid nodes a launch updates.  Reported for the sweep at the default
 #: tile only.
-TRAFFIC_PER_FLUID_NODE = {"fp32": 187.61, "fp16": 126.32}
+TRAFFIC_PER_FLUID_NODE = {"fp32": 187.61, "fp16": 126.32, "bf16": None}
 
 
 def load_peaks():
@@ -323,7 +323,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--precision", default="fp16", choices=["fp16", "fp32"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--compare", default="fp32",
                     help="second precision timed for the mixed-vs-FP32 ratio"
                          " ('none' to skip)")

@@ -63,7 +63,7 @@ typedef enum {
  * the deposit and the growth test are FP64 in both. */
 typedef enum {
     LBM_FP32 = 0, /* populations stored as FP32 */
-    LBM_FP16 = 1  /* populations stored as FP16 deviations from per-node
+    LBM_FP16 = 1, /* populations stored as FP16 deviations from per-node
                      references exact in FP32: per component, direction i
                      reads back f_i / w_i = rho~ + e_i . v + 2^-10 d_i, with
                      rho~ = f_0 / w_0 (the rest population, FP32) and v,
@@ -78,6 +78,10 @@ typedef enum {
                      references take up the rounding of the deviations, so
                      each node keeps its mass to FP32 rounding.  15 32-bit
                      words per node against FP32's 22. */
+    LBM_BF16 = 2  /* as LBM_FP16 with BF16 (8-bit significand, FP32's
+                     exponent range) in place of FP16 for the deviations
+                     and the linear term: the same layout and bytes, eight
+                     times coarser rounding of the deviations. */
 } lbm_precision;
 
 /* Geometry and initial state of one lattice.  Arrays are row-major ny*nx,

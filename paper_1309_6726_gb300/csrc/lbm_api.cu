@@ -18,14 +18,15 @@
 #include "lbm_device.cuh"
 
 namespace lbmk {
+// store: 0 FP32, 1 FP16, 2 BF16 storage
 cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
-                               int ty, bool half, cudaStream_t s);
+                               int ty, int store, cudaStream_t s);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mask_maps,
                             const CUtensorMap *out_maps, const TileRec *sched,
-                            int nslots, int grid, int tx, int ty, bool half,
+                            int nslots, int grid, int tx, int ty, int store,
                             int *err, cudaStream_t s);
-cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid);
+cudaError_t grid_step_tma(int tx, int ty, int store, int *grid);
 int tma_box_x(int tx);
 int tma_mask_box_x(int tx);
 __global__ void k_unstream(const LatDesc *, int, const float *,
@@ -67,7 +68,10 @@ static_assert(sizeof(lbm_obs) == 8 * 16 + 4 * 2 + 8, "lbm_obs layout");
 
 struct lbm_handle {
     int count = 0;
-    bool half = false;
+    bool half = false;  // 16-bit storage (FP16 or BF16): the 15-word layout
+    bool bf16 = false;  // its format
+    // 0 FP32, 1 FP16, 2 BF16 (the step kernels' storage policy)
+    int store() const { return half ? (bf16 ? 2 : 1) : 0; }
     // tile of the step kernel (LBM_TILE overrides, lbm_autotune picks per
     // workload); set by pick_tile
     int tx = 64, ty = 8;
@@ -180,7 +184,8 @@ static bool valid_params(const lbm_params &p, std::string &why) {
         why = "m_threshold must be > 0";
         return false;
     }
-    if (p.precision != LBM_FP32 && p.precision != LBM_FP16) {
+    if (p.precision != LBM_FP32 && p.precision != LBM_FP16 &&
+        p.precision != LBM_BF16) {
         why = "unknown precision";
         return false;
     }
@@ -388,7 +393,7 @@ static size_t plan_tiles(const int32_t *nx, const int32_t *ny, int count,
 
 static bool make_schedule(lbm_handle *h, std::string &why) {
     int grid = 0;
-    cudaError_t e = grid_step_tma(h->tx, h->ty, h->half, &grid);
+    cudaError_t e = grid_step_tma(h->tx, h->ty, h->store(), &grid);
     if (e != cudaSuccess || grid <= 0) {
         why = std::string("TMA kernel setup: ") + cudaGetErrorString(e);
         return false;
@@ -488,7 +493,8 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     lbm_handle *h = new (std::nothrow) lbm_handle();
     if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation");
     h->count = count;
-    h->half = p[0].precision == LBM_FP16;
+    h->half = p[0].precision != LBM_FP32;
+    h->bf16 = p[0].precision == LBM_BF16;
     pick_tile(h);
 
     // ---- packed ragged layout ------------------------------------------
@@ -533,7 +539,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
         d.body_x = (float)P.body_force_x;
         d.m_th = P.m_threshold;
         d.index = l;
-        d.pad_ = 0;
+        d.bf16 = h->bf16 ? 1 : 0;
         h->max_nodes = std::max(h->max_nodes, (size_t)G.nx * G.ny);
         h->in_off_host[l + 1] = h->in_off_host[l] + (int64_t)G.nx * G.ny;
     }
@@ -767,7 +773,7 @@ static cudaError_t launch_tma(lbm_handle *h) {
     const int c = h->count, in = h->cur, out = h->cur ^ 1;
     return launch_step_tma(step_args(h), h->d_maps + in * c, h->d_mask_maps,
                            h->d_maps + (2 + out) * c, h->d_sched, h->sched_slots,
-                           h->sched_grid, h->tx, h->ty, h->half, h->d_err,
+                           h->sched_grid, h->tx, h->ty, h->store(), h->d_err,
                            h->stream);
 }
 
@@ -775,7 +781,7 @@ static cudaError_t launch_one(lbm_handle *h) {
     StepArgs a = step_args(h);
     return h->use_tma
                ? launch_tma(h)
-               : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
+               : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->store(), h->stream);
 }
 
 // Steps per captured graph: even, so a replay starts and ends with the
@@ -830,7 +836,7 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
         cudaError_t e =
             h->use_tma
                 ? launch_tma(h)
-                : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->half, h->stream);
+                : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->store(), h->stream);
         if (e == cudaErrorInvalidValue && k == 0)
             return fail(h, LBM_EINVAL, "unsupported tile shape");
         CK(h, e);
@@ -995,7 +1001,7 @@ static const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '5'};
 
 struct CkptHeader {
     char magic[8];
-    int32_t count, half;
+    int32_t count, half;  // half: the storage, 0 FP32, 1 FP16, 2 BF16
     int64_t pop_elems, node_elems, nsec, steps;
     int32_t cur, pad;
 };
@@ -1008,7 +1014,7 @@ extern "C" lbm_status lbm_save(lbm_handle *h, const char *path) {
     CkptHeader hd;
     memcpy(hd.magic, kMagic, 8);
     hd.count = h->count;
-    hd.half = h->half;
+    hd.half = h->store();
     hd.pop_elems = h->pop_elems;
     hd.node_elems = h->node_elems;
     hd.nsec = h->nsec;
@@ -1052,7 +1058,7 @@ extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
     if (!f) return fail(h, LBM_EIO, std::string("cannot open ") + path);
     CkptHeader hd;
     bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, kMagic, 8) == 0;
-    ok = ok && hd.count == h->count && hd.half == (int)h->half &&
+    ok = ok && hd.count == h->count && hd.half == h->store() &&
          hd.pop_elems == h->pop_elems && hd.node_elems == h->node_elems &&
          hd.nsec == h->nsec;
     std::vector<LatDesc> dsc(h->count);

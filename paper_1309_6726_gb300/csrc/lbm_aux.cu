@@ -13,25 +13,40 @@
 namespace lbmk {
 
 // Stored value q (0..21: A, B, solute) of node offset e, in the
-// populations' own units (FP16 storage: read back and unscaled).
-__device__ __forceinline__ float load_pop(const void *base, const LatDesc &d,
-                                          bool half, int q, int64_t e) {
-    if (!half) return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
-    const uint32_t *w = static_cast<const uint32_t *>(base) + d.pop_off;
+// populations' own units (16-bit storage: read back and unscaled).
+template <class F>
+__device__ __forceinline__ float load_pop16(const uint32_t *w, const LatDesc &d,
+                                            int q, int64_t e) {
     const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
     if (q < 2 * Q) {
         const int comp = q < Q ? 0 : 1, i = q - comp * Q;
         const float r = ref[comp * d.plane + e];
         if (i == 0) return wq(0) * r;
         const int sh = comp ? 16 : 0;  // B in the high halves
-        const float ri = ref_dir(i, false, r, (uint16_t)(w[W16_VEL * d.plane + e] >> sh),
-                                 (uint16_t)(w[(W16_VEL + 1) * d.plane + e] >> sh));
-        return wq(i) * fma_h((uint16_t)(w[(i - 1) * d.plane + e] >> sh),
-                             kH_InvDevScale, ri);
+        const float ri = ref_dir<F>(i, false, r, (uint16_t)(w[W16_VEL * d.plane + e] >> sh),
+                                    (uint16_t)(w[(W16_VEL + 1) * d.plane + e] >> sh));
+        return wq(i) * F::fma((uint16_t)(w[(i - 1) * d.plane + e] >> sh),
+                              F::kInvDevScale, ri);
     }
     const int k = q - 2 * Q;
-    return 0.25f * dec_sol16(w[(W16_SOL + (k >> 1)) * d.plane + e], k,
-                             ref[2 * d.plane + e]);
+    return 0.25f * dec_sol16<F>(w[(W16_SOL + (k >> 1)) * d.plane + e], k,
+                                ref[2 * d.plane + e]);
+}
+__device__ __forceinline__ float load_pop(const void *base, const LatDesc &d,
+                                          bool half, int q, int64_t e) {
+    if (!half) return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
+    const uint32_t *w = static_cast<const uint32_t *>(base) + d.pop_off;
+    return d.bf16 ? load_pop16<BF16>(w, d, q, e) : load_pop16<F16>(w, d, q, e);
+}
+
+// The 15 stored words of a node from its scaled values, in the lattice's
+// 16-bit format.
+__device__ __forceinline__ void enc_node16_d(const LatDesc &d, const float2 f[Q],
+                                             const float gh[QS], uint32_t v[NW16]) {
+    if (d.bf16)
+        enc_node16<BF16>(f, gh, v);
+    else
+        enc_node16<F16>(f, gh, v);
 }
 
 // Post-streaming populations of node (x, y) at the current step: 22 values
@@ -77,7 +92,7 @@ __device__ __forceinline__ void store_node(void *fout, const LatDesc &d,
         f[i] = make_float2(__fdiv_rn(v[i], wq(i)), __fdiv_rn(v[Q + i], wq(i)));
     for (int k = 0; k < QS; ++k) gh[k] = 4.0f * v[2 * Q + k];
     uint32_t wv[NW16];
-    enc_node16(f, gh, wv);
+    enc_node16_d(d, f, gh, wv);
     store_words16(static_cast<uint32_t *>(fout) + d.pop_off + own, pl, wv);
 }
 
@@ -205,7 +220,7 @@ __global__ void k_init_rest_all(const LatDesc *desc, int count,
             for (int i = 0; i < Q; ++i) f[i] = make_float2(ra[src[i]], rb[src[i]]);
             for (int k = 0; k < QS; ++k) gv[k] = cc[ssrc[k]];
             uint32_t wv[NW16];
-            enc_node16(f, gv, wv);
+            enc_node16_d(d, f, gv, wv);
             uint32_t *out = static_cast<uint32_t *>(fout) + d.pop_off;
             store_words16(out + own, (int)d.plane, wv);
             for_ghosts(x, y, d.nx, d.ny, d.pitch, (int)own,
@@ -384,6 +399,29 @@ struct ObsPart {
     int h, nonfin, lo, hi;
 };
 
+template <class F>
+__device__ __forceinline__ void stored_sums16(const void *fin,
+                                              const LatDesc &d, int64_t own,
+                                              float &sa, float &sb, float &sc) {
+    const uint32_t *w = static_cast<const uint32_t *>(fin) + d.pop_off;
+    const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
+    const float2 r = make_float2(ref[own], ref[d.plane + own]);
+    sa = wq(0) * r.x;
+    sb = wq(0) * r.y;
+    const uint32_t wx = w[W16_VEL * d.plane + own];
+    const uint32_t wy = w[(W16_VEL + 1) * d.plane + own];
+    for (int i = 1; i < Q; ++i) {
+        const float2 f = dec_pair<F>(i, false, w[(i - 1) * d.plane + own], r, wx, wy);
+        sa += wq(i) * f.x;
+        sb += wq(i) * f.y;
+    }
+    const float rc = ref[2 * d.plane + own];
+    const uint32_t w01 = w[W16_SOL * d.plane + own];
+    const uint32_t w23 = w[(W16_SOL + 1) * d.plane + own];
+    sc = 0.f;
+    for (int k = 0; k < QS; ++k)
+        sc += 0.25f * dec_sol16<F>(k < 2 ? w01 : w23, k, rc);
+}
 // Sum of the 22 stored values of a node (A, B, solute), as readers decode
 // them (the values load_pop returns, summed in the same order; FP16
 // storage reads each packed word and each reference once).
@@ -395,23 +433,10 @@ __device__ __forceinline__ void stored_sums(const void *fin,
     sb = 0.f;
     sc = 0.f;
     if (half) {
-        const uint32_t *w = static_cast<const uint32_t *>(fin) + d.pop_off;
-        const float *ref = reinterpret_cast<const float *>(w + W16_REF * d.plane);
-        const float2 r = make_float2(ref[own], ref[d.plane + own]);
-        sa = wq(0) * r.x;
-        sb = wq(0) * r.y;
-        const uint32_t wx = w[W16_VEL * d.plane + own];
-        const uint32_t wy = w[(W16_VEL + 1) * d.plane + own];
-        for (int i = 1; i < Q; ++i) {
-            const float2 f = dec_pair(i, false, w[(i - 1) * d.plane + own], r, wx, wy);
-            sa += wq(i) * f.x;
-            sb += wq(i) * f.y;
-        }
-        const float rc = ref[2 * d.plane + own];
-        const uint32_t w01 = w[W16_SOL * d.plane + own];
-        const uint32_t w23 = w[(W16_SOL + 1) * d.plane + own];
-        for (int k = 0; k < QS; ++k)
-            sc += 0.25f * dec_sol16(k < 2 ? w01 : w23, k, rc);
+        if (d.bf16)
+            stored_sums16<BF16>(fin, d, own, sa, sb, sc);
+        else
+            stored_sums16<F16>(fin, d, own, sa, sb, sc);
         return;
     }
     for (int i = 0; i < Q; ++i) {

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -95,7 +96,7 @@ struct alignas(16) LatDesc {
     float g_coh, g_ads, k_r, c_in, body_x;
     double m_th;
     int32_t index;      // position of this lattice in the batch
-    int32_t pad_;
+    int32_t bf16;       // 16-bit storage: 1 BF16, 0 FP16 (unused for FP32)
 };
 static_assert(sizeof(LatDesc) == 128, "LatDesc is copied as 128 bytes");
 
@@ -151,7 +152,7 @@ struct InPtrs {
 constexpr int GHOST = 2;  // ghost rows on each side in y
 constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 
-// ---- FP16 storage codec ------------------------------------------------------
+// ---- 16-bit storage codec (FP16, or BF16) -------------------------------------
 // FP16 storage keeps, per node, the populations in scaled form -- f^_i =
 // f_i / w_i for the D2Q9 components (the equilibrium is then
 // rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u) with no weight) and g^_k = 4 g_k
@@ -208,12 +209,15 @@ constexpr int OBS_ROWS = 4;  // warps per block of k_obs_columns (32 columns)
 // The solute does the same with weights 1/4.  Readers round every
 // read-back exactly as written here (explicit fused multiply-adds), so
 // all code paths rebuild the same FP32 values from the same bits.
+//
+// BF16 in place of FP16 (LBM_BF16): the same layout, scale and steps with
+// an 8-bit significand, so each deviation rounds eight times more
+// coarsely; its wider exponent range is not needed here (the scaled
+// deviations stay far inside FP16's range).  The mass closure is the
+// same; the per-value error grows with the significand.
 constexpr float kDevScale = 1024.0f;
 constexpr float kInvDevScale = 1.0f / 1024.0f;
 
-__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
-    return *reinterpret_cast<uint32_t *>(&h);
-}
 __device__ __forceinline__ uint16_t lo16(uint32_t w) { return (uint16_t)(w & 0xFFFFu); }
 __device__ __forceinline__ uint16_t hi16(uint32_t w) { return (uint16_t)(w >> 16); }
 
@@ -233,27 +237,52 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return __ffma2_rn(a, b, c);
 }
 
-// c + h s for FP16 h and s, FP32 c: the product is exact, the sum rounded
-// once (the mixed-precision fused multiply-add of sm_100-family GPUs, so no
-// separate conversion of h is needed).
-__device__ __forceinline__ float fma_h(uint16_t h, uint16_t s, float c) {
-    float r;
-    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(h), "h"(s), "f"(c));
-    return r;
-}
-constexpr uint16_t kH_InvDevScale = 0x1400;  // 2^-10 in FP16
-constexpr uint16_t kH_One = 0x3C00;          // 1 in FP16
-constexpr uint16_t kH_MinusOne = 0xBC00;     // -1 in FP16
+// The two 16-bit formats of the deviations: FP16 (11-bit significand,
+// the default) and BF16 (8-bit significand, FP32's exponent range).  Both
+// use the same layout, scale and read-back; each provides the packing of
+// a pair, the mixed-precision fused multiply-add c + h s (FP32 c, 16-bit h
+// and s: the product exact, the sum rounded once -- the mixed-precision
+// FMA of sm_100-family GPUs, so no separate conversion of h is needed),
+// and the 16-bit constants 2^-10, 1 and -1.
+struct F16 {
+    static constexpr uint16_t kInvDevScale = 0x1400;  // 2^-10
+    static constexpr uint16_t kOne = 0x3C00;
+    static constexpr uint16_t kMinusOne = 0xBC00;
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    static __device__ __forceinline__ float fma(uint16_t h, uint16_t s, float c) {
+        float r;
+        asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(h), "h"(s), "f"(c));
+        return r;
+    }
+};
+struct BF16 {
+    static constexpr uint16_t kInvDevScale = 0x3A80;  // 2^-10
+    static constexpr uint16_t kOne = 0x3F80;
+    static constexpr uint16_t kMinusOne = 0xBF80;
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    static __device__ __forceinline__ float fma(uint16_t h, uint16_t s, float c) {
+        float r;
+        asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(r) : "h"(h), "h"(s), "f"(c));
+        return r;
+    }
+};
 
 // Reference r_i = rho~ + e_i . v of direction i (1..8) for one component,
-// v's FP16 bits vx, vy: one mixed fused multiply-add per nonzero component
-// of e_i, x first.  flip: the direction opp(i) instead (e = -e_i; the
-// bounced-back value of a pull, a select when i is a constant).
+// v's 16-bit values vx, vy: one mixed fused multiply-add per nonzero
+// component of e_i, x first.  flip: the direction opp(i) instead (e =
+// -e_i; the bounced-back value of a pull, a select when i is a constant).
+template <class F>
 __device__ __forceinline__ float ref_dir(int i, bool flip, float rho,
                                          uint16_t vx, uint16_t vy) {
     float r = rho;
-    if (cx(i) != 0) r = fma_h(vx, (cx(i) > 0) != flip ? kH_One : kH_MinusOne, r);
-    if (cy(i) != 0) r = fma_h(vy, (cy(i) > 0) != flip ? kH_One : kH_MinusOne, r);
+    if (cx(i) != 0) r = F::fma(vx, (cx(i) > 0) != flip ? F::kOne : F::kMinusOne, r);
+    if (cy(i) != 0) r = F::fma(vy, (cy(i) > 0) != flip ? F::kOne : F::kMinusOne, r);
     return r;
 }
 
@@ -261,21 +290,24 @@ __device__ __forceinline__ float ref_dir(int i, bool flip, float rho,
 // deviations w, the source's references {rho~_A, rho~_B} and its
 // linear-reference words wx, wy (a word the direction does not use is not
 // read): r_i + 2^-10 d, rounded as the writer rounds.
+template <class F>
 __device__ __forceinline__ float2 dec_pair(int i, bool flip, uint32_t w,
                                            float2 ref, uint32_t wx,
                                            uint32_t wy) {
     return make_float2(
-        fma_h(lo16(w), kH_InvDevScale, ref_dir(i, flip, ref.x, lo16(wx), lo16(wy))),
-        fma_h(hi16(w), kH_InvDevScale, ref_dir(i, flip, ref.y, hi16(wx), hi16(wy))));
+        F::fma(lo16(w), F::kInvDevScale, ref_dir<F>(i, flip, ref.x, lo16(wx), lo16(wy))),
+        F::fma(hi16(w), F::kInvDevScale, ref_dir<F>(i, flip, ref.y, hi16(wx), hi16(wy))));
 }
 // Solute direction k from the word of its pair (k even: low half).
+template <class F>
 __device__ __forceinline__ float dec_sol16(uint32_t w, int k, float ref) {
-    return fma_h((k & 1) ? hi16(w) : lo16(w), kH_InvDevScale, ref);
+    return F::fma((k & 1) ? hi16(w) : lo16(w), F::kInvDevScale, ref);
 }
 
 // Encodes the scaled post-collision {A, B} values f[0..8] into the 8
 // direction words w[0..7], the linear-reference words wv[0..1] (x, y) and
 // the references {rho~_A, rho~_B} (mass-exact, see above).
+template <class F>
 __device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8],
                                          uint32_t wv[2]) {
     // v for the component with the larger rest population (the majority
@@ -285,20 +317,20 @@ __device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8],
     const float2 vy = mul2(f2s(0.5f), sub2(f[2], f[4]));
     const bool ua = f[0].x >= f[0].y && fabsf(vx.x) + fabsf(vy.x) <= f[0].x;
     const bool ub = f[0].y >= f[0].x && fabsf(vx.y) + fabsf(vy.y) <= f[0].y;
-    wv[0] = h2_bits(__floats2half2_rn(ua ? vx.x : 0.f, ub ? vx.y : 0.f));
-    wv[1] = h2_bits(__floats2half2_rn(ua ? vy.x : 0.f, ub ? vy.y : 0.f));
+    wv[0] = F::pack(ua ? vx.x : 0.f, ub ? vx.y : 0.f);
+    wv[1] = F::pack(ua ? vy.x : 0.f, ub ? vy.y : 0.f);
     float2 e = f2s(0.f);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const float2 r = make_float2(ref_dir(i, false, f[0].x, lo16(wv[0]), lo16(wv[1])),
-                                     ref_dir(i, false, f[0].y, hi16(wv[0]), hi16(wv[1])));
+        const float2 r = make_float2(ref_dir<F>(i, false, f[0].x, lo16(wv[0]), lo16(wv[1])),
+                                     ref_dir<F>(i, false, f[0].y, hi16(wv[0]), hi16(wv[1])));
         // f^_i - r_i is exact where the two are within a factor of two
         // (everywhere the deviation is small), the scale exact
         const float2 dv = mul2(sub2(f[i], r), f2s(kDevScale));
-        const uint32_t h = h2_bits(__floats2half2_rn(dv.x, dv.y));
-        // the quantisation errors dv - FP16(dv), exact
-        const float2 q = make_float2(fma_h(lo16(h), kH_MinusOne, dv.x),
-                                     fma_h(hi16(h), kH_MinusOne, dv.y));
+        const uint32_t h = F::pack(dv.x, dv.y);
+        // the quantisation errors dv - round(dv), exact
+        const float2 q = make_float2(F::fma(lo16(h), F::kMinusOne, dv.x),
+                                     F::fma(hi16(h), F::kMinusOne, dv.y));
         e = fma2(f2s(wq(i)), q, e);
         w[i - 1] = h;
     }
@@ -306,6 +338,7 @@ __device__ __forceinline__ float2 enc_ab(const float2 f[Q], uint32_t w[8],
 }
 
 // Encodes the 4 scaled solute values into two words and the reference.
+template <class F>
 __device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
                                         uint32_t &w23, float &rc) {
     const float c = 0.25f * __fadd_rn(__fadd_rn(gh[0], gh[2]),
@@ -314,25 +347,26 @@ __device__ __forceinline__ void enc_sol(const float gh[QS], uint32_t &w01,
     float d[QS];
 #pragma unroll
     for (int k = 0; k < QS; ++k) d[k] = __fmaf_rn(gh[k], kDevScale, n);
-    w01 = h2_bits(__floats2half2_rn(d[0], d[1]));
-    w23 = h2_bits(__floats2half2_rn(d[2], d[3]));
-    // the quantisation errors d_k - FP16(d_k), exact
+    w01 = F::pack(d[0], d[1]);
+    w23 = F::pack(d[2], d[3]);
+    // the quantisation errors d_k - round(d_k), exact
     const float e = __fadd_rn(
-        __fadd_rn(fma_h(lo16(w01), kH_MinusOne, d[0]),
-                  fma_h(hi16(w01), kH_MinusOne, d[1])),
-        __fadd_rn(fma_h(lo16(w23), kH_MinusOne, d[2]),
-                  fma_h(hi16(w23), kH_MinusOne, d[3])));
+        __fadd_rn(F::fma(lo16(w01), F::kMinusOne, d[0]),
+                  F::fma(hi16(w01), F::kMinusOne, d[1])),
+        __fadd_rn(F::fma(lo16(w23), F::kMinusOne, d[2]),
+                  F::fma(hi16(w23), F::kMinusOne, d[3])));
     rc = __fmaf_rn(e, 0.25f * kInvDevScale, c);
 }
 
 // The 15 stored words of a node from its scaled post-collision values, in
 // plane order (8 direction pairs, 2 solute pairs, 2 linear-reference
 // pairs, rho~_A, rho~_B, C~).
+template <class F>
 __device__ __forceinline__ void enc_node16(const float2 f[Q], const float gh[QS],
                                            uint32_t v[NW16]) {
     float rc;
-    const float2 r = enc_ab(f, v, v + W16_VEL);
-    enc_sol(gh, v[W16_SOL], v[W16_SOL + 1], rc);
+    const float2 r = enc_ab<F>(f, v, v + W16_VEL);
+    enc_sol<F>(gh, v[W16_SOL], v[W16_SOL + 1], rc);
     v[W16_REF] = __float_as_uint(r.x);
     v[W16_REF + 1] = __float_as_uint(r.y);
     v[W16_REF + 2] = __float_as_uint(rc);

@@ -15,9 +15,9 @@ namespace lbmk {
 //
 // Store32: plain FP32 planes, collision in the populations themselves.
 //
-// Store16: FP16 deviations from per-node references (FP32 rest population
-// plus an FP16 linear term), A and B of one direction packed in one half2
-// word (enc_node16 / dec_pair in
+// Store16<F>: 16-bit deviations (F = F16 or BF16) from per-node references
+// (FP32 rest population plus a 16-bit linear term), A and B of one
+// direction packed in one 32-bit word (enc_node16 / dec_pair in
 // lbm_device.cuh); the collision works on the scaled populations f_i / w_i
 // and 4 g_k (fluid_update16).
 // ---------------------------------------------------------------------------
@@ -25,11 +25,14 @@ namespace lbmk {
 struct Store32 {
     static constexpr bool kHalf = false;
     using T = float;
+    using Fmt = F16;  // unused (no 16-bit values)
     static constexpr int kPlanes = NPOP;
 };
+template <class F>
 struct Store16 {
     static constexpr bool kHalf = true;
     using T = uint32_t;
+    using Fmt = F;
     static constexpr int kPlanes = NW16;
 };
 
@@ -297,7 +300,8 @@ __device__ __forceinline__ float2 rcp2_guard(float2 x, float lim) {
     return make_float2(x.x > lim ? r.x : 0.f, x.y > lim ? r.y : 0.f);
 }
 
-// Everything after the pull for a node fluid in s_t, FP16 storage.
+// Everything after the pull for a node fluid in s_t, 16-bit storage of
+// format F.
 //   f, g: scaled post-streaming {A, B} populations and solute of the node;
 //   rho: its densities {rho_A, rho_B} (dens2 of f, as in the density frame);
 //   nb: densities {rho_A, rho_B} at x + e_i (index 1..8; 0 if solid);
@@ -306,7 +310,7 @@ __device__ __forceinline__ float2 rcp2_guard(float2 x, float lim) {
 // formed for both components at once.  put(words) writes the node's 15
 // stored words; its periodic images in the ghost band are written here.
 // Returns true if the node reached the threshold in this step.
-template <class Put>
+template <class F, class Put>
 __device__ __forceinline__ bool fluid_update16(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
     int own, float2 f[Q], float g[QS], float2 rho, const float2 nb[Q],
@@ -375,7 +379,7 @@ __device__ __forceinline__ bool fluid_update16(
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
     uint32_t v[NW16];
-    enc_node16(f, g, v);
+    enc_node16<F>(f, g, v);
     put(v);
     // periodic images in the ghost band
     uint32_t *out = static_cast<uint32_t *>(a.fout) + d.pop_off;

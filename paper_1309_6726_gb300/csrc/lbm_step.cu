@@ -83,8 +83,9 @@ __device__ __forceinline__ void pull4(const float *__restrict__ fin,
     }
 }
 
-// FP16 storage: the scaled {A, B} populations pulled into node (gx, gy)
-// (bb: bounce-back bits of the 9 directions).
+// 16-bit storage (format F): the scaled {A, B} populations pulled into
+// node (gx, gy) (bb: bounce-back bits of the 9 directions).
+template <class F>
 __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
                                          const LatDesc &d, int gx, int gxm,
                                          int gxp, int gy, int gym, int gyp,
@@ -102,7 +103,7 @@ __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
         const int qi = b ? opp(i) : i;
         const uint32_t wx = cx(i) != 0 ? __ldg(w + W16_VEL * d.plane + src) : 0u;
         const uint32_t wy = cy(i) != 0 ? __ldg(w + (W16_VEL + 1) * d.plane + src) : 0u;
-        f[i] = dec_pair(i, b, __ldg(w + (qi - 1) * d.plane + src),
+        f[i] = dec_pair<F>(i, b, __ldg(w + (qi - 1) * d.plane + src),
                         make_float2(__ldg(ref + src), __ldg(ref + d.plane + src)),
                         wx, wy);
     }
@@ -110,6 +111,7 @@ __device__ __forceinline__ void pull16ab(const uint32_t *__restrict__ fin,
 
 // FP16 storage: the 4 scaled solute populations of node (gx, gy) (bb4:
 // bounce-back bits of the 4 directions).
+template <class F>
 __device__ __forceinline__ void pull16s(const uint32_t *__restrict__ fin,
                                         const LatDesc &d, int gx, int gxm,
                                         int gxp, int gy, int gym, int gyp,
@@ -124,7 +126,7 @@ __device__ __forceinline__ void pull16s(const uint32_t *__restrict__ fin,
         const bool b = (bb4 >> k) & 1u;
         const int64_t src = b ? own : (int64_t)syy * d.pitch + sxx;
         const int qk = b ? sopp(k) : k;
-        g[k] = dec_sol16(__ldg(w + (W16_SOL + (qk >> 1)) * d.plane + src), qk,
+        g[k] = dec_sol16<F>(__ldg(w + (W16_SOL + (qk >> 1)) * d.plane + src), qk,
                          __ldg(ref + src));
     }
 }
@@ -147,8 +149,8 @@ __device__ __forceinline__ float2 pull_ab(const StepArgs &a, const LatDesc &d,
         for (int i = 0; i < Q; ++i) { ra += fA[i]; rb += fB[i]; }
         return make_float2(ra, rb);
     } else {
-        pull16ab(static_cast<const uint32_t *>(a.fin), d, gx, gxm, gxp, gy,
-                 gym, gyp, bb, f2);
+        pull16ab<typename S::Fmt>(static_cast<const uint32_t *>(a.fin), d, gx,
+                                  gxm, gxp, gy, gym, gyp, bb, f2);
         return dens2(f2);
     }
 }
@@ -162,8 +164,8 @@ __device__ __forceinline__ void pull_sol(const StepArgs &a, const LatDesc &d,
         pull4(static_cast<const float *>(a.fin), d, gx, gxm, gxp, gy, gym, gyp,
               bb4, g);
     else
-        pull16s(static_cast<const uint32_t *>(a.fin), d, gx, gxm, gxp, gy,
-                gym, gyp, bb4, g);
+        pull16s<typename S::Fmt>(static_cast<const uint32_t *>(a.fin), d, gx,
+                                 gxm, gxp, gy, gym, gyp, bb4, g);
 }
 
 template <class S, int TX, int TY>
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(TX *TY)
                 float2 nbv[Q];
 #pragma unroll
                 for (int i = 1; i < Q; ++i) nbv[i] = make_float2(rAn[i], rBn[i]);
-                flagged = fluid_update16(
+                flagged = fluid_update16<typename S::Fmt>(
                     a, d, l, t, gx, gy, own, f2, g, rho, nbv, snb, ns,
                     [&](const uint32_t *v) {
                         store_words16(static_cast<uint32_t *>(a.fout) + d.pop_off + own,
@@ -297,23 +299,26 @@ __global__ void __launch_bounds__(TX *TY)
 // ---------------------------------------------------------------------------
 
 template <int TX, int TY>
-static cudaError_t launch_tile(const StepArgs &a, int ntiles, bool half,
+static cudaError_t launch_tile(const StepArgs &a, int ntiles, int store,
                                cudaStream_t s) {
-    if (half)
-        k_step<Store16, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+    if (store == 2)
+        k_step<Store16<BF16>, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+    else if (store == 1)
+        k_step<Store16<F16>, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
     else
         k_step<Store32, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
     return cudaGetLastError();
 }
 
+// store: 0 FP32, 1 FP16, 2 BF16 storage
 cudaError_t launch_step_direct(const StepArgs &a, int ntiles, int tx,
-                               int ty, bool half, cudaStream_t s) {
-    if (tx == 32 && ty == 8) return launch_tile<32, 8>(a, ntiles, half, s);
-    if (tx == 32 && ty == 4) return launch_tile<32, 4>(a, ntiles, half, s);
-    if (tx == 32 && ty == 16) return launch_tile<32, 16>(a, ntiles, half, s);
-    if (tx == 64 && ty == 4) return launch_tile<64, 4>(a, ntiles, half, s);
-    if (tx == 64 && ty == 8) return launch_tile<64, 8>(a, ntiles, half, s);
-    if (tx == 128 && ty == 4) return launch_tile<128, 4>(a, ntiles, half, s);
+                               int ty, int store, cudaStream_t s) {
+    if (tx == 32 && ty == 8) return launch_tile<32, 8>(a, ntiles, store, s);
+    if (tx == 32 && ty == 4) return launch_tile<32, 4>(a, ntiles, store, s);
+    if (tx == 32 && ty == 16) return launch_tile<32, 16>(a, ntiles, store, s);
+    if (tx == 64 && ty == 4) return launch_tile<64, 4>(a, ntiles, store, s);
+    if (tx == 64 && ty == 8) return launch_tile<64, 8>(a, ntiles, store, s);
+    if (tx == 128 && ty == 4) return launch_tile<128, 4>(a, ntiles, store, s);
     return cudaErrorInvalidValue;
 }
 

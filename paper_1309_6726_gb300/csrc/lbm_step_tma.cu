@@ -135,7 +135,8 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src,
 
 template <class S, int TX_, int TY_>
 struct TmaTile {
-    using T = typename S::T;  // 32-bit words: FP32 values or FP16 pairs
+    using T = typename S::T;  // 32-bit words: FP32 values or 16-bit pairs
+    using Fmt = typename S::Fmt;  // 16-bit format (16-bit storage)
     static constexpr int TX = TX_, TY = TY_;
     static constexpr int NT = TX * TY;
     static constexpr int NW = NT / 32;            // warps
@@ -239,7 +240,7 @@ __device__ __forceinline__ void spull16ab(const uint32_t *tile, int c,
         const int qi = b ? opp(i) : i;
         const uint32_t wx = cx(i) != 0 ? tile[W16_VEL * TT::PL + cell] : 0u;
         const uint32_t wy = cy(i) != 0 ? tile[(W16_VEL + 1) * TT::PL + cell] : 0u;
-        f[i] = dec_pair(i, b, tile[(qi - 1) * TT::PL + cell],
+        f[i] = dec_pair<typename TT::Fmt>(i, b, tile[(qi - 1) * TT::PL + cell],
                         make_float2(ref[cell], ref[TT::PL + cell]), wx, wy);
     }
 }
@@ -255,7 +256,8 @@ __device__ __forceinline__ void spull16s(const uint32_t *tile, int c,
         const bool b = BB && ((bb >> (k + 1)) & 1u);
         const int cell = b ? c : c - sy(k) * TT::BX - sx(k);
         const int qk = b ? sopp(k) : k;
-        g[k] = dec_sol16(tile[(W16_SOL + (qk >> 1)) * TT::PL + cell], qk, ref[cell]);
+        g[k] = dec_sol16<typename TT::Fmt>(tile[(W16_SOL + (qk >> 1)) * TT::PL + cell], qk,
+                                           ref[cell]);
     }
 }
 
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
                     for (int i = 1; i < Q; ++i)
                         nbv[i] = reinterpret_cast<const float2 *>(fr)[
                             (ly + 1 + cy(i)) * TT::RX + lx + 1 + cx(i)];
-                    flagged = fluid_update16(
+                    flagged = fluid_update16<typename S::Fmt>(
                         a, d, l, t, x, y, own, f2, g, rho, nbv, snb, ns,
                         [&](const uint32_t *v) {
                             if (ts_tile)
@@ -695,11 +697,14 @@ static cudaError_t launch_tma_t(const StepArgs &a, const TmaMaps &mp,
 
 // Persistent grid of the TMA step kernel for a tile shape (also sets its
 // shared-memory limit); 0 on an unsupported shape.
-cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
+// store: 0 FP32, 1 FP16, 2 BF16 storage
+cudaError_t grid_step_tma(int tx, int ty, int store, int *grid) {
     *grid = 0;
 #define LBM_TMA_GRID(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
-        return half ? grid_tma_t<Store16, X, Y>(grid) : grid_tma_t<Store32, X, Y>(grid);
+        return store == 2   ? grid_tma_t<Store16<BF16>, X, Y>(grid)          \
+               : store == 1 ? grid_tma_t<Store16<F16>, X, Y>(grid)           \
+                            : grid_tma_t<Store32, X, Y>(grid);
     LBM_TMA_SHAPES(LBM_TMA_GRID)
 #undef LBM_TMA_GRID
     return cudaErrorInvalidValue;
@@ -708,15 +713,19 @@ cudaError_t grid_step_tma(int tx, int ty, bool half, int *grid) {
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *pop_maps,
                             const CUtensorMap *mask_maps,
                             const CUtensorMap *out_maps, const TileRec *sched,
-                            int nslots, int grid, int tx, int ty, bool half,
+                            int nslots, int grid, int tx, int ty, int store,
                             int *err, cudaStream_t s) {
     const TmaMaps mp{pop_maps, mask_maps, out_maps};
 #define LBM_TMA_CASE(X, Y)                                                   \
     if (tx == X && ty == Y)                                                  \
-        return half ? launch_tma_t<Store16, X, Y>(a, mp, sched, nslots, grid, \
-                                                  err, s)                    \
-                    : launch_tma_t<Store32, X, Y>(a, mp, sched, nslots, grid, \
-                                                  err, s);
+        return store == 2                                                    \
+                   ? launch_tma_t<Store16<BF16>, X, Y>(a, mp, sched, nslots, \
+                                                       grid, err, s)         \
+               : store == 1                                                  \
+                   ? launch_tma_t<Store16<F16>, X, Y>(a, mp, sched, nslots,  \
+                                                      grid, err, s)          \
+                   : launch_tma_t<Store32, X, Y>(a, mp, sched, nslots, grid, \
+                                                 err, s);
     LBM_TMA_SHAPES(LBM_TMA_CASE)
 #undef LBM_TMA_CASE
     return cudaErrorInvalidValue;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(PKG, "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENAN, LBM_EIO = \
     range(7)
-LBM_FP32, LBM_FP16 = 0, 1
+LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2
 FIELD_POPS, FIELD_DEPOSIT, FIELD_DENSITY = 0, 1, 2
 NPOP = 22
 
@@ -147,7 +147,8 @@ class Solver:
     ``geoms`` are :class:`paper_1309_6726_gb300.inputs.Geometry` objects (or
     anything with ``solid``, ``rho_a``, ``rho_b``, ``conc``, ``cap_x0``,
     ``cap_x1``) and ``params`` matching :class:`inputs.ModelParams` (or
-    dicts).  ``precision`` is ``"fp32"`` or ``"fp16"``.
+    dicts).  ``precision`` is ``"fp32"``, ``"fp16"`` or ``"bf16"`` (the
+    16-bit formats share one layout).
     """
 
     def __init__(self, geoms, params, precision: str = "fp32"):
@@ -156,7 +157,7 @@ class Solver:
         if len(geoms) != len(params) or not geoms:
             raise ValueError("need as many params as geometries (>= 1)")
         self._lib = load_library()
-        prec = {"fp32": LBM_FP32, "fp16": LBM_FP16}[precision]
+        prec = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}[precision]
         self.precision = precision
         self._keep = []
         G = (Geometry * len(geoms))()

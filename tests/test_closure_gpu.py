@@ -85,7 +85,7 @@ def test_narrow_capillary_closes_at_the_oracle_step(precision, tol, rtol):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
 def test_batch_closes_each_lattice_at_its_own_step(precision):
     # Four capillaries in one handle: three close at different steps, one
     # (wide, slow reaction) stays open.  The per-lattice closure minimum and

@@ -48,7 +48,7 @@ def test_bounded_wait_times_out_with_a_status(monkeypatch):
     s2.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
 def test_non_finite_lattice_is_flagged_alone(precision):
     # A batch of two capillaries; one gets a NaN population (a blown-up
     # state).  Observables report LBM_ENAN, flag that lattice only, and the

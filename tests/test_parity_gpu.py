@@ -160,7 +160,7 @@ def test_batch_matches_independent_lattices():
         assert obs[k]["delta_e"] == oo["delta_e"]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
 def test_checkpoint_continues_bit_for_bit(tmp_path, precision):
     # FP16 checkpoints carry the deviations, the FP16 references and the
     # FP32 rest planes
@@ -319,7 +319,7 @@ def _batch3():
     return list(geoms), mps
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
 def test_variants_graphs_and_autotune_bit_identical(monkeypatch, precision):
     # Every step-kernel variant (direct loads or TMA tiles, any tile shape),
     # stepping through captured graphs or plain launches, and the autotuned
