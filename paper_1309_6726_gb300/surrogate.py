@@ -185,6 +185,16 @@ def decode(y, t_max):
     return z, closure.astype(np.int64)
 
 
+def spread_of(ys, t_max) -> np.ndarray:
+    """Disagreement of an ensemble per run, in the units of the front error
+    (compare_to_solver): the mean over the times of the members' standard
+    deviation of the front, over the mean predicted front at the last time
+    (at least 10 lattice units).  ys: (members, runs, outputs)."""
+    zs = np.stack([decode(y, t_max)[0] for y in ys])
+    scale = np.maximum(zs.mean(axis=0)[:, -1], 10.0)
+    return zs.std(axis=0).mean(axis=1) / scale
+
+
 def compare_to_solver(z_pred, c_pred, z_lb, c_lb, t_max):
     """Errors of the surrogate against the solver on the same runs.
 
@@ -288,6 +298,15 @@ class Surrogate:
             out += net.forward(xd)
         return (out / len(self.nets)).cpu().numpy()
 
+    def predict_with_spread(self, x, t_max):
+        """The mean prediction and, per run, the members' disagreement
+        (spread_of)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+        ys = np.stack([net.forward(xd).cpu().numpy() for net in self.nets])
+        return self.predict(x), spread_of(ys, t_max)
+
     def params(self):
         return [net.params() for net in self.nets]
 
@@ -296,18 +315,24 @@ class Surrogate:
             net.close()
 
 
-def predict_or_solve(model: Surrogate, members, t_grid, length=L_RANGE):
+def predict_or_solve(model: Surrogate, members, t_grid, length=L_RANGE,
+                     max_spread=None):
     """Answers from the network inside the training domain (parameter box
-    and length range) and from the solver (the fallback) outside it;
-    returns (front, closure, source)."""
+    and length range) and, where max_spread is given, where the ensemble's
+    members agree (spread_of at most max_spread); from the solver (the
+    fallback) elsewhere.  Returns (front, closure, source)."""
     t_max = int(t_grid[-1])
     inside = in_domain(members, length)
     z = np.full((len(members), len(t_grid)), np.nan)
     c = np.full(len(members), -1, np.int64)
     if inside.any():
-        zi, ci = decode(model.predict(features(
-            [m for m, o in zip(members, inside) if o], length)), t_max)
-        z[inside], c[inside] = zi, ci
+        yi, sp = model.predict_with_spread(features(
+            [m for m, o in zip(members, inside) if o], length), t_max)
+        zi, ci = decode(yi, t_max)
+        idx = np.flatnonzero(inside)
+        z[idx], c[idx] = zi, ci
+        if max_spread is not None:
+            inside[idx[sp > max_spread]] = False
     if (~inside).any():
         r = run_trajectories([m for m, o in zip(members, inside) if not o], t_grid)
         z[~inside], c[~inside] = r["z"], r["closure"]
@@ -370,6 +395,24 @@ def main(argv=None):
     t_net = time.perf_counter() - t0
     zp, cp = decode(yp, args.steps)
     res = compare_to_solver(zp, cp, te["z"], te["closure"], args.steps)
+    # with the solver as fallback where the members disagree (the threshold:
+    # the 95th percentile of the spread over the training inputs, no
+    # held-out information): the routed runs are solved again, timed
+    _, sp_train = model.predict_with_spread(x, args.steps)
+    thr = float(np.quantile(sp_train, 0.95))
+    _, sp = model.predict_with_spread(xt, args.steps)
+    routed = sp > thr
+    zf, cf, t_fb = zp.copy(), cp.copy(), t_net
+    if routed.any():
+        r = run_trajectories([m for m, o in zip(test_m, routed) if o], grid)
+        zf[routed], cf[routed] = r["z"], r["closure"]
+        t_fb = t_net + r["seconds"]
+    res_fb = compare_to_solver(zf, cf, te["z"], te["closure"], args.steps)
+    res_fb.update({"max_spread": thr, "routed_runs": int(routed.sum()),
+                   "routed_share": float(routed.mean()),
+                   "seconds": t_fb,
+                   "speedup_vs_solver": (te["seconds"] / t_fb
+                                         if np.isfinite(te["seconds"]) else None)})
     if args.save:
         np.save(args.save, np.stack(model.params()))
     out = {
@@ -387,6 +430,7 @@ def main(argv=None):
         "network_seconds_held_out": t_net,
         "speedup_vs_solver": te["seconds"] / max(t_net, 1e-9),
         "vs_solver": res,
+        "with_fallback": res_fb,
     }
     print(json.dumps(out))
     model.close()

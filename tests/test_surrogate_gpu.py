@@ -59,6 +59,20 @@ def test_surrogate_learns_solver_trajectories_and_saves_time():
     np.testing.assert_array_equal(c[:3], ref["closure"])
     zn, cn = S.decode(model.predict(S.features(test_m[:2], length)), steps)
     np.testing.assert_array_equal(z[3:], zn)
+    # inside the domain, where the members disagree by more than
+    # max_spread, the solver answers too: the runs with the largest spread
+    # go to it, the others keep the network's answer
+    _, sp = model.predict_with_spread(S.features(test_m[:6], length), steps)
+    thr = float(np.sort(sp)[-3])  # the three largest spreads exceed it or equal it
+    z2, c2, src2 = S.predict_or_solve(model, test_m[:6], grid, length,
+                                      max_spread=thr - 1e-12)
+    routed = sp > thr - 1e-12
+    assert list(src2) == ["solver" if r else "network" for r in routed]
+    assert routed.sum() >= 3
+    ref2 = S.run_trajectories([m for m, r in zip(test_m[:6], routed) if r], grid)
+    np.testing.assert_array_equal(z2[routed], ref2["z"])
+    zn2, _ = S.decode(model.predict(S.features(test_m[:6], length)), steps)
+    np.testing.assert_array_equal(z2[~routed], zn2[~routed])
     print("nonfinite runs: train %d/%d, held-out %d/%d, fallback %d/3" % (
         tr["nonfinite"].sum(), len(train_m), te["nonfinite"].sum(),
         len(test_m), ref["nonfinite"].sum()))

@@ -98,3 +98,23 @@ def test_compare_to_solver_by_hand():
     assert r["closure_runs_both"] == 1
     assert r["closure_rel_err_mean"] == pytest.approx(0.1)
     assert r["closure_agreement"] == 1.0
+
+
+def test_spread_is_the_members_front_std_over_the_error_scale():
+    # two members whose fronts decode to 20 and 22 lu at every time: std 1,
+    # mean last front 21 -> 1 / 21; fronts of 1 and 3 lu: std 1 over the
+    # 10 lu floor -> 0.1; identical members -> 0
+    t_max = 1000
+    n_t = S.N_TIMES
+
+    def member(z):
+        y = np.zeros((1, n_t + 1), np.float32)
+        y[0, :n_t] = np.arcsinh(z / S.Z_SCALE)
+        return y
+
+    ys = np.stack([member(20.0), member(22.0)])
+    assert S.spread_of(ys, t_max)[0] == pytest.approx(1 / 21, rel=1e-5)
+    ys = np.stack([member(1.0), member(3.0)])
+    assert S.spread_of(ys, t_max)[0] == pytest.approx(0.1, rel=1e-5)
+    ys = np.stack([member(15.0), member(15.0)])
+    assert S.spread_of(ys, t_max)[0] == 0.0
