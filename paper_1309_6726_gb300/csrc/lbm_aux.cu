@@ -115,6 +115,30 @@ __device__ __forceinline__ int lattice_of(const int64_t *pre, int count,
     return lo;
 }
 
+// Copies n values from src (readable by the device) to dst, 16 bytes per
+// read where src is 16-byte aligned (the reads cross the host link; the
+// device-side writes stay element-wise, dst having no such alignment),
+// element by element otherwise and for the tail; the block's threads
+// stride over [i0, n) with step `step` in units of 16-byte groups.
+template <class T>
+__device__ __forceinline__ void gather_array(const T *src, T *dst, int64_t n,
+                                             int64_t i0, int64_t step) {
+    constexpr int V = 16 / sizeof(T);  // values per 16-byte read
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int64_t nv = n / V;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        for (int64_t q = i0; q < nv; q += step) {
+            const uint4 v = s4[q];
+            const T *t = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int j = 0; j < V; ++j) dst[q * V + j] = t[j];
+        }
+        done = nv * V;
+    }
+    for (int64_t k = done + i0; k < n; k += step) dst[k] = src[k];
+}
+
 // Gathers the inputs of lattices [l0, l0 + gridDim.y) into the device
 // staging area in one launch, reading the caller's arrays where the device
 // can address them (blockIdx.y: the lattice; the blocks in x stride over
@@ -127,13 +151,12 @@ __global__ void k_gather_inputs(const InPtrs *ptr, int l0,
     const InPtrs p = ptr[l];
     const int64_t o = in_off[l], n = in_off[l + 1] - o;
     float *r = rho3 + 3 * o;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        if (p.rho_a) r[k] = p.rho_a[k];
-        if (p.rho_b) r[n + k] = p.rho_b[k];
-        if (p.conc) r[2 * n + k] = p.conc[k];
-        if (p.solid) sol[o + k] = p.solid[k];
-    }
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    if (p.rho_a) gather_array(p.rho_a, r, n, i0, step);
+    if (p.rho_b) gather_array(p.rho_b, r + n, n, i0, step);
+    if (p.conc) gather_array(p.conc, r + 2 * n, n, i0, step);
+    if (p.solid) gather_array(p.solid, sol + o, n, i0, step);
 }
 
 // Mask bytes over every lattice's ghost band (columns -2 .. nx + 1, rows
