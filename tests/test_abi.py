@@ -132,6 +132,7 @@ def test_create_rejects_degenerate_parameters_without_touching_the_gpu(lib):
         (geo(nx=0), params(), b"nx >= 1"),
         (geo(x0=5, x1=5), params(), b"section"),
         (geo(nx=20000, ny=20000), params(), b"too large"),
+        (geo(), params(precision=3), b"unknown precision"),
     ]
     for g, p, msg in cases:
         assert L.lbm_create(ctypes.byref(g), ctypes.byref(p),
@@ -143,3 +144,8 @@ def test_create_rejects_degenerate_parameters_without_touching_the_gpu(lib):
     assert L.lbm_create_batch(G2, P2, 2, ctypes.byref(h)) == lbm.LBM_EINVAL
     assert b"mixed precision" in L.lbm_last_error(None)
     assert L.lbm_create_batch(G2, P2, 0, ctypes.byref(h)) == lbm.LBM_EINVAL
+    # FP16 and BF16 share a layout but not a codec: not mixed either
+    P3 = (lbm.Params * 2)(lbm._params(I.ModelParams().as_dict(), lbm.LBM_FP16),
+                          lbm._params(I.ModelParams().as_dict(), lbm.LBM_BF16))
+    assert L.lbm_create_batch(G2, P3, 2, ctypes.byref(h)) == lbm.LBM_EINVAL
+    assert b"mixed precision" in L.lbm_last_error(None)
