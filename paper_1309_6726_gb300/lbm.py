@@ -36,11 +36,11 @@ class LbmError(RuntimeError):
 
 
 class Geometry(C.Structure):
+    # the arrays as plain addresses (lbm_geometry's typed pointers have the
+    # same representation); integers are quicker to marshal than casts
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
-                ("solid", C.POINTER(C.c_uint8)),
-                ("rho_a", C.POINTER(C.c_float)),
-                ("rho_b", C.POINTER(C.c_float)),
-                ("conc", C.POINTER(C.c_float)),
+                ("solid", C.c_void_p), ("rho_a", C.c_void_p),
+                ("rho_b", C.c_void_p), ("conc", C.c_void_p),
                 ("cap_x0", C.c_int32), ("cap_x1", C.c_int32)]
 
 
@@ -162,7 +162,6 @@ class Solver:
         self._keep = []
         G = (Geometry * len(geoms))()
         P = (Params * len(geoms))()
-        u8p, fp = C.POINTER(C.c_uint8), C.POINTER(C.c_float)
         self.shapes = []
         for k, (g, p) in enumerate(zip(geoms, params)):
             solid = np.ascontiguousarray(g.solid, dtype=np.uint8)
@@ -178,9 +177,8 @@ class Solver:
                     raise ValueError("lattice %d: %s has shape %s, solid %s"
                                      % (k, name, a.shape, solid.shape))
             self._keep += [solid, ra, rb, cc]
-            G[k] = Geometry(nx, ny, C.cast(solid.ctypes.data, u8p),
-                            C.cast(ra.ctypes.data, fp), C.cast(rb.ctypes.data, fp),
-                            C.cast(cc.ctypes.data, fp), int(g.cap_x0),
+            G[k] = Geometry(nx, ny, solid.ctypes.data, ra.ctypes.data,
+                            rb.ctypes.data, cc.ctypes.data, int(g.cap_x0),
                             int(g.cap_x1))
             P[k] = _params(p, prec)
             self.shapes.append((ny, nx))

@@ -108,8 +108,7 @@ def test_create_rejects_degenerate_parameters_without_touching_the_gpu(lib):
     def arr(a, t):
         a = np.ascontiguousarray(a, t)
         keep.append(a)
-        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8 if t == np.uint8
-                                               else ctypes.c_float))
+        return a.ctypes.data
 
     def geo(nx=geom.nx, ny=geom.ny, x0=geom.cap_x0, x1=geom.cap_x1):
         return lbm.Geometry(nx, ny, arr(geom.solid, np.uint8),

@@ -84,16 +84,13 @@ def test_device_resident_inputs_give_the_same_state():
     keep = []
     G = (lbm.Geometry * len(geoms))()
     P = (lbm.Params * len(geoms))()
-    u8p, fp = C.POINTER(C.c_uint8), C.POINTER(C.c_float)
     for k, (g, p) in enumerate(zip(geoms, mps)):
         arrs = [torch.from_numpy(np.ascontiguousarray(getattr(g, name), t)).to(dev)
                 for name, t in ARRAYS]
         keep += arrs
         ny, nx = g.solid.shape
-        G[k] = lbm.Geometry(nx, ny, C.cast(arrs[0].data_ptr(), u8p),
-                            C.cast(arrs[1].data_ptr(), fp),
-                            C.cast(arrs[2].data_ptr(), fp),
-                            C.cast(arrs[3].data_ptr(), fp),
+        G[k] = lbm.Geometry(nx, ny, arrs[0].data_ptr(), arrs[1].data_ptr(),
+                            arrs[2].data_ptr(), arrs[3].data_ptr(),
                             int(g.cap_x0), int(g.cap_x1))
         P[k] = lbm._params(p, lbm.LBM_FP16)
     h = C.c_void_p()
