@@ -230,10 +230,14 @@ def time_e2e(geoms, params, precision, steps, observe_every):
     """Whole job through the C ABI with host buffers: create (host->device
     copy of geometry and initial fields from pinned host memory), steps,
     observables read back every `observe_every` steps and at the end, final
-    solid masks of every lattice read back (one call)."""
+    solid masks of every lattice read back (one call, into pinned host
+    memory)."""
     import torch
     from paper_1309_6726_gb300 import lbm
     geoms = pinned(geoms)
+    # the masks come back into pinned memory, as the inputs go from it
+    masks = torch.empty(sum(g.solid.size for g in geoms), dtype=torch.uint8,
+                        pin_memory=True).numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s = lbm.Solver(geoms, params, precision)
@@ -243,9 +247,9 @@ def time_e2e(geoms, params, precision, steps, observe_every):
         k = min(observe_every, steps - done)
         s.step(k)
         done += k
-        s.observables(allow_nan=True)
+        s.observables_array(allow_nan=True)
         n_obs += 1
-    s.solid_masks()
+    s.solid_masks(out=masks)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     s.close()

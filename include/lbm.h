@@ -179,7 +179,10 @@ lbm_status lbm_set_stream(lbm_handle *h, void *cuda_stream);
 /* Advances every lattice by n >= 0 time steps of the paper's Sec. II
  * update (collision with the Martys-Chen forces, streaming with half-way
  * bounce-back, solute advection-diffusion, surface reaction, deposit and
- * growth; readings c1-c12).  Asynchronous on the bound stream. */
+ * growth; readings c1-c12).  Asynchronous on the bound stream.  The last
+ * step of a call (n > 0) also adds up each lattice's fluid content (rho_A,
+ * rho_B and C over the nodes it updates), which the next lbm_observables
+ * then reads instead of every node's populations. */
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
 /* Number of completed steps. */
@@ -189,7 +192,12 @@ int64_t lbm_step_count(const lbm_handle *h);
 int32_t lbm_count(const lbm_handle *h);
 
 /* Observables of every lattice: out[count].  Synchronizes.  Returns
- * LBM_ENAN (after filling out) if some lattice holds a non-finite value. */
+ * LBM_ENAN (after filling out) if some lattice holds a non-finite value.
+ * The fluid content (mass_a, mass_b, mass_c) comes from the totals of the
+ * last lbm_step call when no call has changed the state since (after
+ * lbm_create, lbm_load, lbm_set_fields or lbm_autotune it sums the stored
+ * populations instead); the two agree to FP32 rounding of each node's
+ * sums. */
 lbm_status lbm_observables(lbm_handle *h, lbm_obs *out);
 
 /* Current solid mask of lattice k (the grown solid of paper Sec. II-III,

@@ -55,11 +55,12 @@ __global__ void k_solid_mask_all(const LatDesc *, int, const int64_t *,
 __global__ void k_obs_columns(const LatDesc *, const int32_t *,
                               const int64_t *, int, const void *,
                               const uint8_t *, const double *, long long,
-                              bool, ColObs *);
+                              bool, bool, ColObs *);
 struct LbmObsDev;
 __global__ void k_obs_reduce(const LatDesc *, const int64_t *,
                              const ColObs *, const int16_t *,
-                             const LatState *, long long, LbmObsDev *);
+                             const LatState *, const double *, long long,
+                             LbmObsDev *);
 }  // namespace lbmk
 
 using namespace lbmk;
@@ -102,6 +103,10 @@ struct lbm_handle {
     unsigned int *d_done = nullptr;
     ColObs *d_cols = nullptr;
     void *d_obs = nullptr;
+    // [count][3] A, B and solute totals that the last launch of each
+    // lbm_step call adds up, valid for step count sums_step
+    double *d_sums = nullptr;
+    int64_t sums_step = -1;
     float *d_canon = nullptr;      // [22][ny][nx] scratch of one lattice
     float *d_dens = nullptr;       // [3][ny][nx]
     double *d_dep = nullptr;       // [ny][nx]
@@ -155,7 +160,7 @@ static void free_all(lbm_handle *h) {
                   h->d_mask, h->d_m, h->d_col_fluid, h->d_wall0, h->d_st,
                   h->d_step, h->d_done, h->d_cols, h->d_obs, h->d_canon,
                   h->d_dens, h->d_dep, h->d_maps, h->d_mask_maps, h->d_err,
-                  h->d_sched};
+                  h->d_sched, h->d_sums};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -581,6 +586,7 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
     AL(h->d_done, 1);
     AL(h->d_cols, cols);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_obs, count * sizeof(lbm_obs));
+    AL(h->d_sums, 3 * count);
     AL(h->d_canon, NPOP * h->max_nodes);
     AL(h->d_dens, 3 * h->max_nodes);
     AL(h->d_dep, h->max_nodes);
@@ -672,22 +678,32 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
             }
         }
     }
+    // tables the kernels read (small synchronous copies on the legacy
+    // stream, which the handle's stream does not wait for)
     bad(cudaMemcpy(h->d_desc, h->desc.data(), count * sizeof(LatDesc), cudaMemcpyHostToDevice), "desc");
     bad(cudaMemcpy(h->d_tile_lat, tile_lat.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
     bad(cudaMemcpy(h->d_col_lat, col_lat.data(), cols * sizeof(int32_t), cudaMemcpyHostToDevice), "cols");
     bad(cudaMemcpy(h->d_col_base, h->col_base.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice), "colbase");
-    bad(cudaMemset(h->d_mask, 0, node), "memset");
-    bad(cudaMemset(h->d_pop[0], 0, pop * esz), "memset");
-    bad(cudaMemset(h->d_pop[1], 0, pop * esz), "memset");
-    bad(cudaMemset(h->d_m, 0, node * sizeof(double)), "memset");
     std::vector<LatState> st0(count);
     for (auto &x : st0) {
         memset(&x, 0, sizeof(x));
         x.closure = ~0ull;
     }
     bad(cudaMemcpy(h->d_st, st0.data(), count * sizeof(LatState), cudaMemcpyHostToDevice), "state");
-    bad(cudaMemset(h->d_step, 0, sizeof(int64_t)), "memset");
-    bad(cudaMemset(h->d_err, 0, sizeof(int)), "memset");
+    // the zeroed buffers on a stream of their own, behind nothing, so that
+    // they run beside the gather; the host meanwhile builds the tensor maps
+    // and the block schedule
+    cudaStream_t s2 = nullptr;
+    bad(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "stream");
+    if (st == LBM_OK) {
+        bad(cudaMemsetAsync(h->d_mask, 0, node, s2), "memset");
+        bad(cudaMemsetAsync(h->d_pop[0], 0, pop * esz, s2), "memset");
+        bad(cudaMemsetAsync(h->d_pop[1], 0, pop * esz, s2), "memset");
+        bad(cudaMemsetAsync(h->d_m, 0, node * sizeof(double), s2), "memset");
+        bad(cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), s2), "memset");
+        bad(cudaMemsetAsync(h->d_err, 0, sizeof(int), s2), "memset");
+        bad(cudaMemsetAsync(h->d_done, 0, sizeof(unsigned), s2), "memset");
+    }
     if (st == LBM_OK && h->use_tma) {
         std::string why;
         if (!make_maps(h, why) || !make_schedule(h, why)) {
@@ -695,10 +711,10 @@ extern "C" lbm_status lbm_create_batch(const lbm_geometry *g,
             st = LBM_ECUDA;
         }
     }
-    bad(cudaMemset(h->d_done, 0, sizeof(unsigned)), "memset");
-    // the memsets above ran on the legacy stream; the handle's stream does
-    // not wait for it
+    // the gather (handle's stream), the zeroing (s2) and the legacy-stream
+    // copies all land before the set-up kernels
     if (st == LBM_OK) bad(cudaDeviceSynchronize(), "sync");
+    if (s2) cudaStreamDestroy(s2);
     if (st == LBM_OK) {
         k_mask_init_all<<<(unsigned)pre_h[2 * C1 + count], 128, 0, s>>>(
             h->d_desc, count, pre + 2 * C1, pre, sol, h->d_mask);
@@ -765,30 +781,36 @@ static StepArgs step_args(lbm_handle *h) {
     a.step = h->d_step;
     a.done = h->d_done;
     a.stall_tx = h->stall_tx;
+    a.sums = nullptr;
     return a;
 }
 
-// One launch of the TMA step kernel reading buffer cur, writing cur ^ 1.
-static cudaError_t launch_tma(lbm_handle *h) {
+// One launch of the step kernel reading buffer cur, writing cur ^ 1.  sum:
+// the launch also adds up the lattice totals (zeroed first, on the stream)
+// that lbm_observables then reads instead of the whole state.
+static cudaError_t launch_one(lbm_handle *h, bool sum) {
+    StepArgs a = step_args(h);
+    if (sum) {
+        cudaError_t e = cudaMemsetAsync(h->d_sums, 0, 3 * h->count * sizeof(double),
+                                        h->stream);
+        if (e != cudaSuccess) return e;
+        a.sums = h->d_sums;
+    }
+    if (!h->use_tma)
+        return launch_step_direct(a, h->ntiles, h->tx, h->ty, h->store(), h->stream);
     const int c = h->count, in = h->cur, out = h->cur ^ 1;
-    return launch_step_tma(step_args(h), h->d_maps + in * c, h->d_mask_maps,
+    return launch_step_tma(a, h->d_maps + in * c, h->d_mask_maps,
                            h->d_maps + (2 + out) * c, h->d_sched, h->sched_slots,
                            h->sched_grid, h->tx, h->ty, h->store(), h->d_err,
                            h->stream);
-}
-
-static cudaError_t launch_one(lbm_handle *h) {
-    StepArgs a = step_args(h);
-    return h->use_tma
-               ? launch_tma(h)
-               : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->store(), h->stream);
 }
 
 // Steps per captured graph: even, so a replay starts and ends with the
 // same population buffer as input.
 static const int kGraphSteps = 16;
 
-// Captures kGraphSteps launches starting from buffer 0 into h->graph.
+// Captures kGraphSteps launches starting from buffer 0 into h->graph; the
+// last one sums the lattice totals.
 static lbm_status capture_graph(lbm_handle *h) {
     const int cur0 = h->cur;
     h->cur = 0;
@@ -796,7 +818,7 @@ static lbm_status capture_graph(lbm_handle *h) {
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-        e = launch_one(h);
+        e = launch_one(h, k == kGraphSteps - 1);
         h->cur ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
@@ -812,13 +834,16 @@ static lbm_status capture_graph(lbm_handle *h) {
 extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
     if (!h || n < 0) return fail(h, LBM_EINVAL, "bad handle or n < 0");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
-    // whole groups of kGraphSteps steps replay one captured graph (the
+    // The last launch of the call adds up the lattice totals of the state it
+    // leaves (so does the last launch of each graph replay).
+    // Whole groups of kGraphSteps steps replay one captured graph (the
     // step count lives on the device, so the graph needs no new arguments)
     // (a pending test stall is never captured into the graph)
+    if (n > 0) h->sums_step = -1;
     while (h->use_graph && h->stall_tx == 0 &&
            n >= kGraphSteps + (h->cur ? 1 : 0)) {
         if (h->cur) {  // one plain step to get back to buffer 0
-            CK(h, launch_one(h));
+            CK(h, launch_one(h, false));
             h->cur ^= 1;
             h->steps += 1;
             n -= 1;
@@ -830,19 +855,17 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
         CK(h, cudaGraphLaunch(h->graph, h->stream));
         h->steps += kGraphSteps;
         n -= kGraphSteps;
+        h->sums_step = h->steps;
     }
     for (int64_t k = 0; k < n; ++k) {
-        StepArgs a = step_args(h);
-        cudaError_t e =
-            h->use_tma
-                ? launch_tma(h)
-                : launch_step_direct(a, h->ntiles, h->tx, h->ty, h->store(), h->stream);
+        cudaError_t e = launch_one(h, k == n - 1);
         if (e == cudaErrorInvalidValue && k == 0)
             return fail(h, LBM_EINVAL, "unsupported tile shape");
         CK(h, e);
         h->stall_tx = 0;  // the test stall applies to one launch
         h->cur ^= 1;
         h->steps += 1;
+        if (k == n - 1) h->sums_step = h->steps;
     }
     return LBM_OK;
 }
@@ -851,13 +874,16 @@ extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
     if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     // 32 columns per block, OBS_ROWS warps splitting their rows
+    // the last step launch summed the stored totals: the column pass then
+    // reads the mask and the nodes that turned solid, not the whole state
+    const bool summed = h->sums_step == h->steps;
     const int nb = (int)((h->ncols + 31) / 32);
     k_obs_columns<<<nb, dim3(32, OBS_ROWS), 0, h->stream>>>(
         h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
-        h->d_mask, h->d_m, h->steps, h->half, h->d_cols);
+        h->d_mask, h->d_m, h->steps, h->half, summed, h->d_cols);
     k_obs_reduce<<<h->count, 256, 0, h->stream>>>(
-        h->d_desc, h->d_col_base, h->d_cols, h->d_wall0, h->d_st, h->steps,
-        (LbmObsDev *)h->d_obs);
+        h->d_desc, h->d_col_base, h->d_cols, h->d_wall0, h->d_st,
+        summed ? h->d_sums : nullptr, h->steps, (LbmObsDev *)h->d_obs);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(out, h->d_obs, h->count * sizeof(lbm_obs),
                           cudaMemcpyDeviceToHost, h->stream));
@@ -897,13 +923,16 @@ extern "C" lbm_status lbm_get_solid_masks(lbm_handle *h, uint8_t *host,
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     const int64_t total = h->in_off_host.back();
     if (n != (size_t)total) return fail(h, LBM_EINVAL, "size mismatch");
+    // device scratch, then one copy (into pinned memory the copy runs at
+    // the link's rate; the kernel writing pinned memory itself measured
+    // slower, 1.07 against 0.77 ms for 105 MB)
     if (!h->d_masks) CK(h, dalloc(&h->d_masks, (size_t)total));
     const MaskBits mb(h->steps);
     k_solid_mask_all<<<(unsigned)h->total_rows, 128, 0, h->stream>>>(
         h->d_desc, h->count, h->d_in_off + h->count + 1, h->d_in_off, h->d_mask,
         mb.force, h->d_masks);
     CK(h, cudaGetLastError());
-    CK(h, cudaMemcpyAsync(host, h->d_masks, n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(host, h->d_masks, n, cudaMemcpyDefault, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -951,6 +980,7 @@ extern "C" lbm_status lbm_set_fields(lbm_handle *h, int32_t k, int32_t which,
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     const LatDesc &d = h->desc[k];
     const size_t N = (size_t)d.nx * d.ny;
+    h->sums_step = -1;  // the last step's lattice totals no longer hold
     if (which == LBM_FIELD_POPS) {
         if (bytes != NPOP * N * 4) return fail(h, LBM_EINVAL, "size mismatch");
         lbm_status s = settle(h, k);
@@ -1094,6 +1124,7 @@ extern "C" lbm_status lbm_load(lbm_handle *h, const char *path) {
     fclose(f);
     if (!ok) return fail(h, LBM_EIO, std::string("read failed: ") + path);
     h->steps = hd.steps;
+    h->sums_step = -1;
     return LBM_OK;
 }
 
@@ -1220,10 +1251,11 @@ extern "C" lbm_status lbm_autotune(lbm_handle *h, int32_t steps,
             best_ms = ms / n;
             best = c;
         }
-        // back to the saved state
+        // back to the saved state (its lattice totals are not kept)
         if (ce == cudaSuccess) ce = copy_all(false);
         h->cur = cur0;
         h->steps = steps0;
+        h->sums_step = -1;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

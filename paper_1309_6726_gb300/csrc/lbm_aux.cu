@@ -49,29 +49,57 @@ __device__ __forceinline__ void enc_node16_d(const LatDesc &d, const float2 f[Q]
         enc_node16<F16>(f, gh, v);
 }
 
+// load_pop for one storage known at compile time (0 FP32, 1 FP16, 2 BF16).
+template <int ST>
+__device__ __forceinline__ float load_pop_st(const void *base, const LatDesc &d,
+                                             int q, int64_t e) {
+    if constexpr (ST == 0) {
+        return static_cast<const float *>(base)[d.pop_off + q * d.plane + e];
+    } else {
+        const uint32_t *w = static_cast<const uint32_t *>(base) + d.pop_off;
+        if constexpr (ST == 2) return load_pop16<BF16>(w, d, q, e);
+        else return load_pop16<F16>(w, d, q, e);
+    }
+}
+
 // Post-streaming populations of node (x, y) at the current step: 22 values
 // (A, B, solute), pulled from the stored post-collision state with the
-// streaming mask bit.
+// streaming mask bit.  (One straight-line body per storage, so that the
+// loads of all directions can be in flight together.)
+template <int ST>
+__device__ __forceinline__ void pull_node_st(const void *fin,
+                                             const uint8_t *mask,
+                                             const LatDesc &d, uint8_t pullbit,
+                                             int x, int y, float out[NPOP]) {
+    const int nx = d.nx, ny = d.ny;
+    const int64_t own = (int64_t)y * d.pitch + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xs = wrap1(x - cx(i), nx), ys = wrap1(y - cy(i), ny);
+        const int64_t src = (int64_t)ys * d.pitch + xs;
+        const bool b = i != 0 && (mask[src] & pullbit);
+        out[i] = load_pop_st<ST>(fin, d, b ? opp(i) : i, b ? own : src);
+        out[Q + i] = load_pop_st<ST>(fin, d, Q + (b ? opp(i) : i), b ? own : src);
+    }
+#pragma unroll
+    for (int k = 0; k < QS; ++k) {
+        const int xs = wrap1(x - sx(k), nx), ys = wrap1(y - sy(k), ny);
+        const int64_t src = (int64_t)ys * d.pitch + xs;
+        const bool b = mask[src] & pullbit;
+        out[2 * Q + k] = load_pop_st<ST>(fin, d, 2 * Q + (b ? sopp(k) : k), b ? own : src);
+    }
+}
 __device__ __forceinline__ void pull_node(const void *fin,
                                           const uint8_t *mask,
                                           const LatDesc &d, bool half,
                                           uint8_t pullbit, int x, int y,
                                           float out[NPOP]) {
-    const int nx = d.nx, ny = d.ny;
-    const int64_t own = (int64_t)y * d.pitch + x;
-    for (int i = 0; i < Q; ++i) {
-        const int xs = wrap1(x - cx(i), nx), ys = wrap1(y - cy(i), ny);
-        const int64_t src = (int64_t)ys * d.pitch + xs;
-        const bool b = i != 0 && (mask[src] & pullbit);
-        out[i] = load_pop(fin, d, half, b ? opp(i) : i, b ? own : src);
-        out[Q + i] = load_pop(fin, d, half, Q + (b ? opp(i) : i), b ? own : src);
-    }
-    for (int k = 0; k < QS; ++k) {
-        const int xs = wrap1(x - sx(k), nx), ys = wrap1(y - sy(k), ny);
-        const int64_t src = (int64_t)ys * d.pitch + xs;
-        const bool b = mask[src] & pullbit;
-        out[2 * Q + k] = load_pop(fin, d, half, 2 * Q + (b ? sopp(k) : k), b ? own : src);
-    }
+    if (!half)
+        pull_node_st<0>(fin, mask, d, pullbit, x, y, out);
+    else if (d.bf16)
+        pull_node_st<2>(fin, mask, d, pullbit, x, y, out);
+    else
+        pull_node_st<1>(fin, mask, d, pullbit, x, y, out);
 }
 
 // Writes the stored form of node (x, y) from its 22 post-collision values
@@ -469,11 +497,15 @@ __device__ __forceinline__ void stored_sums(const void *fin,
     for (int k = 0; k < QS; ++k) sc += load_pop(fin, d, half, 2 * Q + k, own);
 }
 
+// summed: the last step launch added up the fluid content of the nodes it
+// updated (StepArgs::sums); the pass then reads the populations only of the
+// nodes that turned solid and of the phase rows.
 __global__ void __launch_bounds__(32 * OBS_ROWS)
     k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
                   const int64_t *col_base, int ncols_total, const void *fin,
                   const uint8_t *mask_all,
-                  const double *m_all, long long t, bool half, ColObs *out) {
+                  const double *m_all, long long t, bool half, bool summed,
+                  ColObs *out) {
     __shared__ ObsPart part[OBS_ROWS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int c = blockIdx.x * 32 + lane;
@@ -486,12 +518,18 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
         const LatDesc d = desc[l];
         const int x = (int)(c - col_base[l]);
         const uint8_t *mask = mask_all + d.node_off;
-        float v[NPOP];
+        const double *mcol = m_all + d.node_off;
+        // mask statistics, deposit and (unless summed) stored content, row
+        // by row; the rows' loads are independent (the deposit is read
+        // whatever the node), so the unrolled loop keeps several in flight
+        bool pending = false;
+#pragma unroll 8
         for (int y = w; y < d.ny; y += OBS_ROWS) {
             const int64_t own = (int64_t)y * d.pitch + x;
             const uint8_t sv = mask[own];
+            const double mv = mcol[own];
             const bool fluid_before = !(sv & mb.pull);
-            if (fluid_before) {
+            if (!summed && fluid_before) {
                 float sa, sb, sc;
                 stored_sums(fin, d, half, own, sa, sb, sc);
                 if (!(sa + sb < 3.0e38f)) p.nonfin = 1;
@@ -500,21 +538,31 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
                 p.stored[2] += sc;
             }
             if (sv & mb.force) {
-                if (fluid_before) {  // turned solid at the end of the last step
-                    pull_node(fin, mask, d, half, mb.pull, x, y, v);
-                    double ra = 0, rb = 0;
-                    for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
-                    p.pend[0] += ra;
-                    p.pend[1] += rb;
-                    p.pend[2] += (double)v[18] + v[19] + v[20] + v[21];
-                    p.pend[3] += m_all[d.node_off + own];
-                }
+                pending |= fluid_before;
                 continue;
             }
-            p.dep += m_all[d.node_off + own];
+            // (FP64 adds are slow on this GPU; most deposits are 0)
+            if (__double_as_longlong(mv) != 0) p.dep += mv;
             p.h += 1;
             p.lo = min(p.lo, y);
             p.hi = max(p.hi, y);
+        }
+        // nodes that turned solid at the end of the last step (few): the
+        // content they received and their deposit
+        if (pending) {
+            float v[NPOP];
+            for (int y = w; y < d.ny; y += OBS_ROWS) {
+                const int64_t own = (int64_t)y * d.pitch + x;
+                const uint8_t sv = mask[own];
+                if (!(sv & mb.force) || (sv & mb.pull)) continue;
+                pull_node(fin, mask, d, half, mb.pull, x, y, v);
+                double ra = 0, rb = 0;
+                for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
+                p.pend[0] += ra;
+                p.pend[1] += rb;
+                p.pend[2] += (double)v[18] + v[19] + v[20] + v[21];
+                p.pend[3] += mcol[own];
+            }
         }
     }
     part[w][lane] = p;
@@ -621,10 +669,12 @@ struct LbmObsDev {  // mirrors lbm_obs of the public header
 };
 
 // blockDim.x must be 256.
+// sums: per lattice {A, B, solute} summed by the last step launch over the
+// nodes it updated (null: the column pass summed the stored state).
 __global__ void k_obs_reduce(const LatDesc *desc, const int64_t *col_base,
                              const ColObs *cols, const int16_t *wall0,
-                             const LatState *st, long long t,
-                             LbmObsDev *out) {
+                             const LatState *st, const double *sums,
+                             long long t, LbmObsDev *out) {
     __shared__ double sh[256];
     __shared__ int s_first[2];
     __shared__ int s_min_h;
@@ -692,6 +742,7 @@ __global__ void k_obs_reduce(const LatDesc *desc, const int64_t *col_base,
     if (tid == 0) {
         LbmObsDev r;
         r.step = t;
+        int nnonfin_any = 0;
         double z[2];
         const int rows[2] = {(ny - 1) / 2, ny / 2};
         for (int k = 0; k < 2; ++k) {
@@ -712,6 +763,15 @@ __global__ void k_obs_reduce(const LatDesc *desc, const int64_t *col_base,
         r.r_h = perim > 0 ? area / perim : 0.0;
         r.delta_e = de;
         const LatState s = st[l];
+        if (sums) {
+            // the updated nodes' content (the column pass left it out of
+            // ma .. mc, which hold minus the nodes that turned solid)
+            const double *q = sums + 3 * l;
+            ma += q[0];
+            mb += q[1];
+            mc += q[2];
+            if (!(q[0] + q[1] < 3.0e38)) nnonfin_any = 1;
+        }
         r.ledger_a = s.ledger[0] + pa;
         r.ledger_b = s.ledger[1] + pb;
         r.ledger_c = s.ledger[2] + pc;
@@ -721,7 +781,7 @@ __global__ void k_obs_reduce(const LatDesc *desc, const int64_t *col_base,
         r.mass_b = mb;
         r.mass_c = mc;
         r.closed = nclosed > 0;
-        r.nonfinite = (nnonfin > 0) || s.nonfinite;
+        r.nonfinite = (nnonfin > 0) || nnonfin_any || s.nonfinite;
         r.closure_step = s.closure == ~0ull ? -1 : (long long)s.closure;
         out[l] = r;
     }

@@ -138,6 +138,17 @@ struct StepArgs {
     // test hook of the bounded waits: bytes that block 0 expects on top of
     // its first tile's copies and that no copy delivers (0 normally)
     int32_t stall_tx;
+    // per lattice {A, B, solute}: this launch adds the fluid content of
+    // every node it updates (zeroed before the launch); null on launches
+    // that do not sum
+    double *sums;
+};
+
+// One node's share of StepArgs::sums: rho_A and rho_B as the collision
+// conserves them (its post-collision populations sum to these up to FP32
+// rounding) and C after the update and the reaction.
+struct NodeTot {
+    float a, b, c;
 };
 
 // One lattice's input arrays (row-major ny * nx) as the device addresses

@@ -169,13 +169,15 @@ __device__ __forceinline__ Shift forces_shift(const LatDesc &d, float rA,
 //   rhoA_nb / rhoB_nb: densities at x + e_i (index 1..8; 0 if solid in s_t);
 //   snb: bit i set if x + e_i is solid in s_t;  ns: solid D2Q4 links.
 // put(fA, fB, g) writes the node's own post-collision values; its periodic
-// images in the ghost band are written here.
+// images in the ghost band are written here.  want: also sets tot to the
+// node's fluid content (NodeTot).
 // Returns true if the node reached the threshold in this step.
 template <class Put>
 __device__ __forceinline__ bool fluid_update(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
     int own, float fA[Q], float fB[Q], float g[QS], const float rhoA_nb[Q],
-    const float rhoB_nb[Q], unsigned snb, int ns, Put put) {
+    const float rhoB_nb[Q], unsigned snb, int ns, Put put, bool want,
+    NodeTot &tot) {
     // ---- moments ----------------------------------------------------------
     float rA, jAx, jAy, rB, jBx, jBy;
     moments9(fA, rA, jAx, jAy);
@@ -202,7 +204,8 @@ __device__ __forceinline__ bool fluid_update(
     }
     // ---- surface reaction, deposit, threshold ----------------------------
     bool flagged = false;
-    if (ns > 0 && rA > rB) {
+    const bool react = ns > 0 && rA > rB;
+    if (react) {
         // fraction of the solute consumed, k_r n_s (capped at all of it);
         // applied as g - g * lost rather than g * (1 - lost) so that
         // rounding 1 - lost does not bias the small consumption
@@ -223,6 +226,11 @@ __device__ __forceinline__ bool fluid_update(
         }
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
+    if (want) {
+        tot.a = rA;
+        tot.b = rB;
+        tot.c = (g[0] + g[2]) + (g[1] + g[3]);
+    }
     put(fA, fB, g);
     // periodic images in the ghost band
     for_ghosts(gx, gy, d.nx, d.ny, d.pitch, own,
@@ -309,12 +317,13 @@ __device__ __forceinline__ float2 rcp2_guard(float2 x, float lim) {
 // The forces and the shift are those of forces_shift (readings c1, c3, c4),
 // formed for both components at once.  put(words) writes the node's 15
 // stored words; its periodic images in the ghost band are written here.
+// want: also sets tot to the node's fluid content (NodeTot).
 // Returns true if the node reached the threshold in this step.
 template <class F, class Put>
 __device__ __forceinline__ bool fluid_update16(
     const StepArgs &a, const LatDesc &d, int l, long long t, int gx, int gy,
     int own, float2 f[Q], float g[QS], float2 rho, const float2 nb[Q],
-    unsigned snb, int ns, Put put) {
+    unsigned snb, int ns, Put put, bool want, NodeTot &tot) {
     float2 jx, jy;
     mom2(f, jx, jy);
     // ---- Martys-Chen forces: A feels B, B feels A -------------------------
@@ -360,7 +369,8 @@ __device__ __forceinline__ bool fluid_update16(
     }
     // ---- surface reaction, deposit, threshold ----------------------------
     bool flagged = false;
-    if (ns > 0 && rho.x > rho.y) {
+    const bool react = ns > 0 && rho.x > rho.y;
+    if (react) {
         const float cs = 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
         const float lost = fminf(1.0f, d.k_r * (float)ns);
 #pragma unroll
@@ -380,6 +390,11 @@ __device__ __forceinline__ bool fluid_update16(
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
     uint32_t v[NW16];
     enc_node16<F>(f, g, v);
+    if (want) {
+        tot.a = rho.x;
+        tot.b = rho.y;
+        tot.c = 0.25f * ((g[0] + g[2]) + (g[1] + g[3]));
+    }
     put(v);
     // periodic images in the ghost band
     uint32_t *out = static_cast<uint32_t *>(a.fout) + d.pop_off;
@@ -428,6 +443,76 @@ __device__ __forceinline__ void retire_node(const StepArgs &a,
     atomicAdd(&a.st[l].ledger[1], rb);
     atomicAdd(&a.st[l].ledger[2], c);
     atomicAdd(&a.st[l].ledger[3], mv);
+}
+
+// Lattice totals of a summing launch.  Each thread keeps running FP32
+// totals of its nodes in the consecutive tiles of one lattice, with the
+// rounding error of every addition carried along (two-sum); when the block
+// moves to another lattice, and at the end of the launch, each warp
+// reduces them the same way and lane 0 adds the result to StepArgs::sums
+// in FP64.  FP64 arithmetic runs at a small fraction of the FP32 rate on
+// this GPU and a warp shuffle takes an issue slot of the whole SM, so
+// neither is on the per-node path.
+
+// s + e = a + b exactly (Knuth's two-sum; round-to-nearest FP32).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+struct TotAcc {
+    float s[3], e[3];  // A, B, solute: sum and accumulated error
+    int l;             // lattice, -1 before the first tile
+};
+
+__device__ __forceinline__ void tot_reset(TotAcc &c, int l) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { c.s[j] = 0.f; c.e[j] = 0.f; }
+    c.l = l;
+}
+
+// Reduces the warp's totals (every lane calls it; after the butterfly all
+// lanes hold the same sums) and lane 0 adds them to its lattice's sums.
+__device__ __forceinline__ void tot_flush(const TotAcc &c, double *sums,
+                                          int lane) {
+    if (c.l < 0) return;
+    float v[3], e[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { v[j] = c.s[j]; e[j] = c.e[j]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float pv = __shfl_xor_sync(0xffffffffu, v[j], o);
+            const float pe = __shfl_xor_sync(0xffffffffu, e[j], o);
+            float r;
+            two_sum(v[j], pv, v[j], r);
+            e[j] = __fadd_rn(__fadd_rn(e[j], pe), r);
+        }
+    if (lane == 0) {
+        double *dst = sums + 3 * c.l;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(dst + j, (double)v[j] + (double)e[j]);
+    }
+}
+
+// Adds this thread's node of a tile of lattice l (every lane of the warp
+// calls it, with the same l).
+__device__ __forceinline__ void tot_add(TotAcc &c, const NodeTot &t, int l,
+                                        double *sums, int lane) {
+    if (l != c.l) {
+        tot_flush(c, sums, lane);
+        tot_reset(c, l);
+    }
+    const float v[3] = {t.a, t.b, t.c};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float r;
+        two_sum(c.s[j], v[j], c.s[j], r);
+        c.e[j] = __fadd_rn(c.e[j], r);
+    }
 }
 
 // The last block of a launch to finish advances the step counter for the

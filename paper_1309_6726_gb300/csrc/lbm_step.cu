@@ -168,7 +168,8 @@ __device__ __forceinline__ void pull_sol(const StepArgs &a, const LatDesc &d,
                                  gxm, gxp, gy, gym, gyp, bb4, g);
 }
 
-template <class S, int TX, int TY>
+// SUM: the launch also adds up the lattice totals (StepArgs::sums).
+template <class S, int TX, int TY, bool SUM>
 __global__ void __launch_bounds__(TX *TY)
     k_step(StepArgs a) {
     using TL = Tile<TX, TY>;
@@ -239,6 +240,8 @@ __global__ void __launch_bounds__(TX *TY)
     }
     __syncthreads();
 
+    constexpr bool want = SUM;
+    NodeTot tot{0.f, 0.f, 0.f};
     if (active) {
         const int own = gy * d.pitch + gx;
         const int hy = ly + 2, hx = lx + 2;
@@ -280,16 +283,24 @@ __global__ void __launch_bounds__(TX *TY)
                     [&](const uint32_t *v) {
                         store_words16(static_cast<uint32_t *>(a.fout) + d.pop_off + own,
                                       (int)d.plane, v);
-                    });
+                    },
+                    want, tot);
             } else {
                 flagged = fluid_update(
                     a, d, l, t, gx, gy, own, fA, fB, g, rAn, rBn, snb, ns,
                     [&](const float *pa, const float *pb, const float *pg) {
                         store_node22(a, d, own, pa, pb, pg);
-                    });
+                    },
+                    want, tot);
             }
             if (flagged) mask_store(mask, own, gx, gy, nx, ny, d.pitch, s_own | mb.next);
         }
+    }
+    if constexpr (SUM) {
+        TotAcc acc;
+        tot_reset(acc, l);
+        tot_add(acc, tot, l, a.sums, tid & 31);
+        tot_flush(acc, a.sums, tid & 31);
     }
     finish_launch(a, t);
 }
@@ -298,15 +309,24 @@ __global__ void __launch_bounds__(TX *TY)
 // Launchers
 // ---------------------------------------------------------------------------
 
+template <int TX, int TY, bool SUM>
+static void launch_tile_t(const StepArgs &a, int ntiles, int store,
+                          cudaStream_t s) {
+    if (store == 2)
+        k_step<Store16<BF16>, TX, TY, SUM><<<ntiles, TX * TY, 0, s>>>(a);
+    else if (store == 1)
+        k_step<Store16<F16>, TX, TY, SUM><<<ntiles, TX * TY, 0, s>>>(a);
+    else
+        k_step<Store32, TX, TY, SUM><<<ntiles, TX * TY, 0, s>>>(a);
+}
+
 template <int TX, int TY>
 static cudaError_t launch_tile(const StepArgs &a, int ntiles, int store,
                                cudaStream_t s) {
-    if (store == 2)
-        k_step<Store16<BF16>, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
-    else if (store == 1)
-        k_step<Store16<F16>, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+    if (a.sums)
+        launch_tile_t<TX, TY, true>(a, ntiles, store, s);
     else
-        k_step<Store32, TX, TY><<<ntiles, TX * TY, 0, s>>>(a);
+        launch_tile_t<TX, TY, false>(a, ntiles, store, s);
     return cudaGetLastError();
 }
 

@@ -364,7 +364,8 @@ struct TmaMaps {
     const CUtensorMap *pop, *mask, *out;
 };
 
-template <class S, int TX, int TY>
+// SUM: the launch also adds up the lattice totals (StepArgs::sums).
+template <class S, int TX, int TY, bool SUM>
 __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
     k_step_tma(StepArgs a, TmaMaps mp, const TileRec *__restrict__ sched,
                int nslots, int *__restrict__ err) {
@@ -457,6 +458,8 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
     };
 
     unsigned parity = 0u;  // bit s: phase parity of stage s
+    TotAcc acc;
+    if constexpr (SUM) tot_reset(acc, -1);
     for (int k = 0; s_rec[k % NSL].lat >= 0; ++k) {
         // the record of the tile NS ahead, fetched now so that its load
         // latency hides behind this tile's work
@@ -599,6 +602,8 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
             if (nxt.lat >= 0) issue(nxt, s, (k + NS) % NSL, 0);
         }
 
+        constexpr bool want = SUM;
+        NodeTot tot{0.f, 0.f, 0.f};
         if (active) {
             const int own = y * d.pitch + x;
             const int lid = ly * TX + lx;
@@ -629,7 +634,8 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
                                 store_words16(static_cast<uint32_t *>(a.fout) +
                                                   d.pop_off + own,
                                               (int)d.plane, v);
-                        });
+                        },
+                        want, tot);
                 } else {
                     float rAn[Q], rBn[Q];
 #pragma unroll
@@ -646,12 +652,14 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
                                             TT::NT, pa, pb, pg);
                             else
                                 store_node22(a, d, own, pa, pb, pg);
-                        });
+                        },
+                        want, tot);
                 }
                 if (flagged)
                     mask_store(a.mask + d.node_off, own, x, y, nx, ny, d.pitch, s_own | mb.next);
             }
         }
+        if constexpr (SUM) tot_add(acc, tot, l, a.sums, lane);
         if constexpr (TT::TS) fence_proxy_async();  // before the next barrier
     }
     if constexpr (TT::TS) {
@@ -661,6 +669,7 @@ __global__ void __launch_bounds__(TX *TY, (TmaTile<S, TX, TY>::MINB))
             bulk_wait_all();
         }
     }
+    if constexpr (SUM) tot_flush(acc, a.sums, lane);
     finish_launch(a, t);
 }
 
@@ -670,13 +679,17 @@ template <class S, int TX, int TY>
 static cudaError_t grid_tma_t(int *grid) {
     using TT = TmaTile<S, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(
-        k_step_tma<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_step_tma<S, TX, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         TT::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_tma<S, TX, TY, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TT::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tma<S, TX, TY>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tma<S, TX, TY, false>,
                                                       TX * TY, TT::SMEM);
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);
@@ -688,8 +701,12 @@ static cudaError_t launch_tma_t(const StepArgs &a, const TmaMaps &mp,
                                 const TileRec *sched, int nslots, int grid,
                                 int *err, cudaStream_t s) {
     using TT = TmaTile<S, TX, TY>;
-    k_step_tma<S, TX, TY><<<grid, TX * TY, TT::SMEM, s>>>(a, mp, sched, nslots,
-                                                          err);
+    if (a.sums)
+        k_step_tma<S, TX, TY, true><<<grid, TX * TY, TT::SMEM, s>>>(a, mp, sched,
+                                                                    nslots, err);
+    else
+        k_step_tma<S, TX, TY, false><<<grid, TX * TY, TT::SMEM, s>>>(a, mp, sched,
+                                                                     nslots, err);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,13 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+#: lbm_obs as a numpy record (the same bytes as Obs)
+OBS_DTYPE = np.dtype([(n, {C.c_int64: np.int64, C.c_int32: np.int32,
+                           C.c_double: np.float64}[t]) for n, t in Obs._fields_],
+                     align=True)
+assert OBS_DTYPE.itemsize == C.sizeof(Obs)
+
+
 _lib = None
 
 
@@ -227,13 +234,21 @@ class Solver:
         return int(self._lib.lbm_step_count(self._h))
 
     # -- outputs -------------------------------------------------------------
+    def observables_array(self, allow_nan: bool = False) -> np.ndarray:
+        """Observables of every lattice as one record array (OBS_DTYPE,
+        the fields of observables())."""
+        out = np.empty(self.count, OBS_DTYPE)
+        st = self._lib.lbm_observables(
+            self._h, out.ctypes.data_as(C.POINTER(Obs)))
+        if not (st == LBM_ENAN and allow_nan):
+            self._check(st)
+        return out
+
     def observables(self, allow_nan: bool = False) -> list[dict]:
-        out = (Obs * self.count)()
-        st = self._lib.lbm_observables(self._h, out)
-        if st == LBM_ENAN and allow_nan:
-            return [o.as_dict() for o in out]
-        self._check(st)
-        return [o.as_dict() for o in out]
+        """Observables of every lattice, one dict each."""
+        a = self.observables_array(allow_nan)
+        names = a.dtype.names
+        return [dict(zip(names, r)) for r in a.tolist()]
 
     def solid_mask(self, k: int = 0) -> np.ndarray:
         ny, nx = self.shapes[k]
@@ -242,10 +257,20 @@ class Solver:
             self._h, k, out.ctypes.data_as(C.POINTER(C.c_uint8)), out.size))
         return out
 
-    def solid_masks(self) -> list[np.ndarray]:
-        """Solid masks of every lattice, read back in one call."""
+    def solid_masks(self, out: np.ndarray | None = None) -> list[np.ndarray]:
+        """Solid masks of every lattice, read back in one call: views of
+        one buffer of all lattices' nodes, ``out`` if given (a contiguous
+        uint8 array of that size, e.g. in pinned memory, where the copy
+        runs at the link's full rate)."""
         sizes = [ny * nx for ny, nx in self.shapes]
-        buf = np.zeros(sum(sizes), np.uint8)
+        if out is None:
+            buf = np.empty(sum(sizes), np.uint8)
+        else:
+            buf = out.reshape(-1)
+            if (buf.dtype != np.uint8 or buf.size != sum(sizes)
+                    or not buf.flags.c_contiguous):
+                raise ValueError("out: need %d contiguous uint8 values"
+                                 % sum(sizes))
         self._check(self._lib.lbm_get_solid_masks(
             self._h, buf.ctypes.data_as(C.POINTER(C.c_uint8)), buf.size))
         out, o = [], 0

@@ -108,3 +108,29 @@ def test_device_resident_inputs_give_the_same_state():
         np.testing.assert_array_equal(s.populations(k), ref.populations(k))
     s.close()
     ref.close()
+
+
+def test_masks_into_pinned_and_pageable_buffers_agree():
+    # The batch's solid masks read back into a new pageable buffer, into a
+    # caller's pinned buffer and lattice by lattice, after growth has
+    # changed them.
+    import torch
+    geoms, mps = _batch()
+    s = lbm.Solver(geoms, mps, "fp16")
+    s.step(400)
+    pageable = s.solid_masks()
+    n = sum(g.solid.size for g in geoms)
+    out = torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy()
+    out[:] = 7  # every byte must be written
+    pinned = s.solid_masks(out=out)
+    for k in range(len(geoms)):
+        single = s.solid_mask(k)
+        np.testing.assert_array_equal(pageable[k], single)
+        np.testing.assert_array_equal(pinned[k], single)
+        assert np.shares_memory(pinned[k], out)
+    assert set(np.unique(out)) <= {0, 1}
+    grown = sum(int(m.sum()) for m in pinned) - sum(int(g.solid.sum()) for g in geoms)
+    print("nodes grown: %d" % grown)
+    with pytest.raises(ValueError):
+        s.solid_masks(out=np.empty(n - 1, np.uint8))
+    s.close()
