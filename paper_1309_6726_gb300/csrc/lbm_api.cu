@@ -52,10 +52,11 @@ __global__ void k_init_rest_all(const LatDesc *, int, const int64_t *,
 __global__ void k_solid_mask_all(const LatDesc *, int, const int64_t *,
                                  const int64_t *, const uint8_t *, uint8_t,
                                  uint8_t *);
-__global__ void k_obs_columns(const LatDesc *, const int32_t *,
-                              const int64_t *, int, const void *,
-                              const uint8_t *, const double *, long long,
-                              bool, bool, ColObs *);
+void launch_obs_columns(bool summed, int store, int nb, int ncols,
+                        const LatDesc *desc, const int32_t *col_lat,
+                        const int64_t *col_base, const void *fin,
+                        const uint8_t *mask, const double *m, long long t,
+                        ColObs *out, cudaStream_t s);
 struct LbmObsDev;
 __global__ void k_obs_reduce(const LatDesc *, const int64_t *,
                              const ColObs *, const int16_t *,
@@ -878,9 +879,9 @@ extern "C" lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
     // reads the mask and the nodes that turned solid, not the whole state
     const bool summed = h->sums_step == h->steps;
     const int nb = (int)((h->ncols + 31) / 32);
-    k_obs_columns<<<nb, dim3(32, OBS_ROWS), 0, h->stream>>>(
-        h->d_desc, h->d_col_lat, h->d_col_base, (int)h->ncols, h->d_pop[h->cur],
-        h->d_mask, h->d_m, h->steps, h->half, summed, h->d_cols);
+    launch_obs_columns(summed, h->store(), nb, (int)h->ncols, h->d_desc,
+                       h->d_col_lat, h->d_col_base, h->d_pop[h->cur], h->d_mask,
+                       h->d_m, h->steps, h->d_cols, h->stream);
     k_obs_reduce<<<h->count, 256, 0, h->stream>>>(
         h->d_desc, h->d_col_base, h->d_cols, h->d_wall0, h->d_st,
         summed ? h->d_sums : nullptr, h->steps, (LbmObsDev *)h->d_obs);

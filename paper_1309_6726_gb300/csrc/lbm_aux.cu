@@ -497,15 +497,17 @@ __device__ __forceinline__ void stored_sums(const void *fin,
     for (int k = 0; k < QS; ++k) sc += load_pop(fin, d, half, 2 * Q + k, own);
 }
 
-// summed: the last step launch added up the fluid content of the nodes it
+// SUMMED: the last step launch added up the fluid content of the nodes it
 // updated (StepArgs::sums); the pass then reads the populations only of the
 // nodes that turned solid and of the phase rows.
-__global__ void __launch_bounds__(32 * OBS_ROWS)
+// ST: the storage (0 FP32, 1 FP16, 2 BF16).
+template <bool SUMMED, int ST>
+__global__ void __launch_bounds__(32 * OBS_ROWS, SUMMED ? 6 : 1)
     k_obs_columns(const LatDesc *desc, const int32_t *col_lat,
                   const int64_t *col_base, int ncols_total, const void *fin,
                   const uint8_t *mask_all,
-                  const double *m_all, long long t, bool half, bool summed,
-                  ColObs *out) {
+                  const double *m_all, long long t, ColObs *out) {
+    constexpr bool half = ST != 0;
     __shared__ ObsPart part[OBS_ROWS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int c = blockIdx.x * 32 + lane;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
             const uint8_t sv = mask[own];
             const double mv = mcol[own];
             const bool fluid_before = !(sv & mb.pull);
-            if (!summed && fluid_before) {
+            if (!SUMMED && fluid_before) {
                 float sa, sb, sc;
                 stored_sums(fin, d, half, own, sa, sb, sc);
                 if (!(sa + sb < 3.0e38f)) p.nonfin = 1;
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
                 const int64_t own = (int64_t)y * d.pitch + x;
                 const uint8_t sv = mask[own];
                 if (!(sv & mb.force) || (sv & mb.pull)) continue;
-                pull_node(fin, mask, d, half, mb.pull, x, y, v);
+                pull_node_st<ST>(fin, mask, d, mb.pull, x, y, v);
                 double ra = 0, rb = 0;
                 for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
                 p.pend[0] += ra;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
         float ph = 0.f;
         if (need) {
             float v[NPOP];
-            pull_node(fin, mask, d, half, mb.pull, x, y, v);
+            pull_node_st<ST>(fin, mask, d, mb.pull, x, y, v);
             float ra = 0.f, rb = 0.f;
             for (int i = 0; i < Q; ++i) { ra += v[i]; rb += v[Q + i]; }
             ph = ra - rb;
@@ -644,6 +646,28 @@ __global__ void __launch_bounds__(32 * OBS_ROWS)
     if (sfl[2][lane]) { o.phi0 = sphi[2][lane]; o.fl0 = 1; }
     if (sfl[3][lane]) { o.phi1 = sphi[3][lane]; o.fl1 = 1; }
     out[c] = o;
+}
+
+// The column pass for a handle's storage and summing state.
+void launch_obs_columns(bool summed, int store, int nb, int ncols,
+                        const LatDesc *desc, const int32_t *col_lat,
+                        const int64_t *col_base, const void *fin,
+                        const uint8_t *mask, const double *m, long long t,
+                        ColObs *out, cudaStream_t s) {
+    const dim3 blk(32, OBS_ROWS);
+#define LBM_OBS(SUM, ST)                                                       \
+    k_obs_columns<SUM, ST><<<nb, blk, 0, s>>>(desc, col_lat, col_base, ncols, \
+                                              fin, mask, m, t, out)
+    if (summed) {
+        if (store == 2) LBM_OBS(true, 2);
+        else if (store == 1) LBM_OBS(true, 1);
+        else LBM_OBS(true, 0);
+    } else {
+        if (store == 2) LBM_OBS(false, 2);
+        else if (store == 1) LBM_OBS(false, 1);
+        else LBM_OBS(false, 0);
+    }
+#undef LBM_OBS
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
