@@ -118,7 +118,9 @@ struct lbm_handle {
     CUtensorMap *d_mask_maps = nullptr; // [count] mask maps
     TileRec *d_sched = nullptr;        // TMA kernel: tiles of each block
     int sched_grid = 0, sched_slots = 0;
-    cudaGraphExec_t graph = nullptr;   // kGraphSteps steps from cur == 0
+    // kGraphSteps steps from cur == 0; [1]: the last launch sums the
+    // lattice totals (the replay that ends an lbm_step call)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool use_graph = true;
     int stall_tx = 0;  // test hook, see pick_tile
     int *d_err = nullptr;              // kernel error flags
@@ -164,7 +166,8 @@ static void free_all(lbm_handle *h) {
                   h->d_sched, h->d_sums};
     for (void *p : ps)
         if (p) cudaFree(p);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaGraphExec_t g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (h->own) cudaStreamDestroy(h->own);
 }
 
@@ -426,9 +429,9 @@ static bool make_schedule(lbm_handle *h, std::string &why) {
 // counts in the descriptors, the tile -> lattice table and, for the TMA
 // kernel, the tensor maps and the block schedule.  Drops the captured graph.
 static lbm_status retile(lbm_handle *h, bool tma, int tx, int ty) {
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
+    for (cudaGraphExec_t &g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
     }
     h->use_tma = tma;
     h->tx = tx;
@@ -810,23 +813,23 @@ static cudaError_t launch_one(lbm_handle *h, bool sum) {
 // same population buffer as input.
 static const int kGraphSteps = 16;
 
-// Captures kGraphSteps launches starting from buffer 0 into h->graph; the
-// last one sums the lattice totals.
-static lbm_status capture_graph(lbm_handle *h) {
+// Captures kGraphSteps launches starting from buffer 0 into h->graph[sum];
+// sum: the last one adds up the lattice totals.
+static lbm_status capture_graph(lbm_handle *h, int sum) {
     const int cur0 = h->cur;
     h->cur = 0;
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-        e = launch_one(h, k == kGraphSteps - 1);
+        e = launch_one(h, sum && k == kGraphSteps - 1);
         h->cur ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     h->cur = cur0;
     CK(h, e);
     CK(h, e2);
-    cudaError_t e3 = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[sum], g, 0);
     cudaGraphDestroy(g);
     CK(h, e3);
     return LBM_OK;
@@ -836,7 +839,8 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
     if (!h || n < 0) return fail(h, LBM_EINVAL, "bad handle or n < 0");
     if (h->dead) return fail(h, LBM_ECUDA, "handle is dead: " + h->err);
     // The last launch of the call adds up the lattice totals of the state it
-    // leaves (so does the last launch of each graph replay).
+    // leaves (a replay that ends the call uses the graph whose last launch
+    // sums).
     // Whole groups of kGraphSteps steps replay one captured graph (the
     // step count lives on the device, so the graph needs no new arguments)
     // (a pending test stall is never captured into the graph)
@@ -849,14 +853,15 @@ extern "C" lbm_status lbm_step(lbm_handle *h, int64_t n) {
             h->steps += 1;
             n -= 1;
         }
-        if (!h->graph) {
-            lbm_status st = capture_graph(h);
+        const int sum = n == kGraphSteps;
+        if (!h->graph[sum]) {
+            lbm_status st = capture_graph(h, sum);
             if (st != LBM_OK) return st;
         }
-        CK(h, cudaGraphLaunch(h->graph, h->stream));
+        CK(h, cudaGraphLaunch(h->graph[sum], h->stream));
         h->steps += kGraphSteps;
         n -= kGraphSteps;
-        h->sums_step = h->steps;
+        if (sum) h->sums_step = h->steps;
     }
     for (int64_t k = 0; k < n; ++k) {
         cudaError_t e = launch_one(h, k == n - 1);
