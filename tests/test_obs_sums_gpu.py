@@ -114,3 +114,23 @@ def test_setting_populations_drops_the_step_totals():
     assert after["mass_a"] == pytest.approx(fluid_a, rel=1e-6)
     assert after["mass_a"] == pytest.approx(1.25 * before["mass_a"], rel=1e-5)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_summing_launches_leave_the_state_unchanged(precision):
+    # every launch summing (one step per call) against one summing launch
+    # in 60 steps: the same populations and masks, bit for bit
+    geoms, mps = _closing_batch()
+    a = lbm.Solver(geoms, mps, precision)
+    b = lbm.Solver(geoms, mps, precision)
+    for _ in range(60):
+        a.step(1)
+    b.step(60)
+    for k in range(len(geoms)):
+        np.testing.assert_array_equal(a.populations(k), b.populations(k))
+        np.testing.assert_array_equal(a.solid_mask(k), b.solid_mask(k))
+    for oa, ob in zip(a.observables(), b.observables()):
+        for key in FLUID_KEYS:
+            assert oa[key] == pytest.approx(ob[key], rel=1e-12)
+    a.close()
+    b.close()
