@@ -67,14 +67,19 @@ GAMMA = 0.144
 
 
 def _fit_window(t, z, t_lo, z_hi):
-    """Indices of the samples in the linear Washburn regime: after t_lo and
-    before the front passes z_hi, finite."""
+    """Indices of the samples in the linear Washburn regime: after t_lo,
+    before the front passes z_hi and up to its farthest advance (a front
+    that stalls, the section narrowing, and then recedes has left the
+    regime), finite."""
     t = np.asarray(t, float)
     z = np.asarray(z, float)
     ok = np.isfinite(z) & (t >= t_lo)
     past = np.flatnonzero(np.isfinite(z) & (z >= z_hi))
     if past.size:
         ok &= np.arange(z.size) < past[0]
+    if ok.any():
+        top = np.flatnonzero(ok)[np.argmax(z[ok])]
+        ok &= np.arange(z.size) <= top
     return np.flatnonzero(ok)
 
 
