@@ -66,13 +66,14 @@ typedef enum {
     LBM_FP16 = 1, /* populations stored as FP16 deviations from per-node
                      references exact in FP32: per component, direction i
                      reads back f_i / w_i = rho~ + e_i . v + 2^-10 d_i, with
-                     rho~ = f_0 / w_0 (the rest population, FP32) and v,
-                     for the component with the larger rest population
-                     and where |v_x| + |v_y| <= rho~, the odd part of the
-                     axis populations ((f^_1 - f^_3) / 2, (f^_2 - f^_4) /
-                     2, rounded to FP16; else 0), so the majority's FP16
-                     d_i holds only the second-order and non-equilibrium
-                     part;
+                     rho~ = f_0 / w_0 (the rest population, FP32) and v
+                     the odd part of the axis populations ((f^_1 -
+                     f^_3) / 2, (f^_2 - f^_4) / 2, rounded to FP16) for
+                     the component with the larger rest population where
+                     |v_x| + |v_y| <= rho~, for the other one at nodes
+                     next to a wall where |v_x| + |v_y| <= 4 rho~, else
+                     0; so d_i holds only the second-order and
+                     non-equilibrium part there;
                      the solute reads back 4 g_k = C~ + 2^-10 d_k.  The A and
                      B values of a direction share one 32-bit word; the
                      references take up the rounding of the deviations, so

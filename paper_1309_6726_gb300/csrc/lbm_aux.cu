@@ -40,13 +40,14 @@ __device__ __forceinline__ float load_pop(const void *base, const LatDesc &d,
 }
 
 // The 15 stored words of a node from its scaled values, in the lattice's
-// 16-bit format.
+// 16-bit format, encoded as for a node away from walls (any choice of the
+// linear reference reads back; the step's encoder gives wall nodes theirs).
 __device__ __forceinline__ void enc_node16_d(const LatDesc &d, const float2 f[Q],
                                              const float gh[QS], uint32_t v[NW16]) {
     if (d.bf16)
-        enc_node16<BF16>(f, gh, v);
+        enc_node16<BF16>(f, gh, v, false);
     else
-        enc_node16<F16>(f, gh, v);
+        enc_node16<F16>(f, gh, v, false);
 }
 
 // load_pop for one storage known at compile time (0 FP32, 1 FP16, 2 BF16).

@@ -389,7 +389,7 @@ __device__ __forceinline__ bool fluid_update16(
     }
     if (!(rt < 3.0e38f)) atomicOr(&a.st[l].nonfinite, 1);
     uint32_t v[NW16];
-    enc_node16<F>(f, g, v);
+    enc_node16<F>(f, g, v, snb != 0u);
     if (want) {
         tot.a = rho.x;
         tot.b = rho.y;

@@ -10,9 +10,11 @@ components and random solute values:
   BF16) of its deviation from the reference (plus FP32 rounding): the deviation is 2^10 (f^_i - r_i),
   r_i = rho~ + e_i . v;
 * v is the odd part of the axis populations for the component with the
-  larger rest population where |v_x| + |v_y| <= f^_0, and 0 otherwise;
-  with it, the deviations of a slow flow are second order in u, so the
-  read-back error of such a node is far below the rest-only reference's.
+  larger rest population where |v_x| + |v_y| <= f^_0, for the other one
+  only at a node next to a wall and where |v_x| + |v_y| <= 4 f^_0, and 0
+  otherwise; with it, the deviations of a slow flow are second order in
+  u, so the read-back error of such a node is far below the rest-only
+  reference's.  Both kinds of node are encoded.
 
 A small test library is compiled from the library's own header with nvcc."""
 import ctypes as C
@@ -32,7 +34,7 @@ using namespace lbmk;
 // read back, gout: n x 4, words: n x NW16
 template <class F>
 __global__ void k(const float2 *f, const float *g, float2 *out, float *gout,
-                  uint32_t *words, int n) {
+                  uint32_t *words, int n, bool wall) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     float2 fv[Q];
@@ -40,7 +42,7 @@ __global__ void k(const float2 *f, const float *g, float2 *out, float *gout,
     for (int i = 0; i < Q; ++i) fv[i] = f[j * Q + i];
     for (int k = 0; k < QS; ++k) gv[k] = g[j * QS + k];
     uint32_t w[NW16];
-    enc_node16<F>(fv, gv, w);
+    enc_node16<F>(fv, gv, w, wall);
     for (int q = 0; q < NW16; ++q) words[j * NW16 + q] = w[q];
     const float2 ref = make_float2(__uint_as_float(w[W16_REF]),
                                    __uint_as_float(w[W16_REF + 1]));
@@ -51,14 +53,14 @@ __global__ void k(const float2 *f, const float *g, float2 *out, float *gout,
     for (int k = 0; k < QS; ++k)
         gout[j * QS + k] = dec_sol16<F>(w[W16_SOL + (k >> 1)], k, rc);
 }
-extern "C" int run(int bf16, const float *f, const float *g, float *out,
-                   float *gout, unsigned *words, int n) {
+extern "C" int run(int bf16, int wall, const float *f, const float *g,
+                   float *out, float *gout, unsigned *words, int n) {
     if (bf16)
         k<BF16><<<(n + 127) / 128, 128>>>((const float2 *)f, g, (float2 *)out, gout,
-                                          (uint32_t *)words, n);
+                                          (uint32_t *)words, n, wall != 0);
     else
         k<F16><<<(n + 127) / 128, 128>>>((const float2 *)f, g, (float2 *)out, gout,
-                                         (uint32_t *)words, n);
+                                         (uint32_t *)words, n, wall != 0);
     return (int)cudaDeviceSynchronize();
 }
 '''
@@ -82,9 +84,9 @@ def codec(tmp_path_factory):
                     "-I", os.path.join(ROOT, "paper_1309_6726_gb300", "csrc"),
                     str(d / "codec.cu"), "-o", so], check=True)
     lib = C.CDLL(so)
-    lib.run.argtypes = [C.c_int] + [C.c_void_p] * 5 + [C.c_int]
+    lib.run.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 5 + [C.c_int]
 
-    def call(f, g, fmt):
+    def call(f, g, fmt, wall):
         n = f.shape[0]
         dev = torch.device("cuda", 0)
         fd = torch.from_numpy(np.ascontiguousarray(f, np.float32)).to(dev)
@@ -92,8 +94,9 @@ def codec(tmp_path_factory):
         out = torch.empty_like(fd)
         gout = torch.empty_like(gd)
         words = torch.empty((n, NW16), dtype=torch.int32, device=dev)
-        assert lib.run(1 if fmt == "bf16" else 0, fd.data_ptr(), gd.data_ptr(),
-                       out.data_ptr(), gout.data_ptr(), words.data_ptr(), n) == 0
+        assert lib.run(1 if fmt == "bf16" else 0, int(wall), fd.data_ptr(),
+                       gd.data_ptr(), out.data_ptr(), gout.data_ptr(),
+                       words.data_ptr(), n) == 0
         return (out.cpu().numpy().astype(np.float64),
                 gout.cpu().numpy().astype(np.float64),
                 words.cpu().numpy().view(np.uint32))
@@ -134,14 +137,15 @@ def _ulp(x, fmt):
     return 2.0 ** (np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** emin))) - m)
 
 
+@pytest.mark.parametrize("wall", [False, True])
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 @pytest.mark.parametrize("u_max", [1e-3, 0.1, 0.6])
-def test_codec_round_trip(codec, u_max, fmt):
+def test_codec_round_trip(codec, u_max, fmt, wall):
     rng = np.random.default_rng(int(u_max * 1e4) + 3)
     n = 20000
     f, rho, a_major = _equilibria(rng, n, u_max)
     g = rng.uniform(0.0, 1.2, (n, 4)).astype(np.float32)
-    out, gout, words = codec(f, g, fmt)
+    out, gout, words = codec(f, g, fmt, wall)
     f64 = f.astype(np.float64)
     # mass of each component: weighted sum of the read-back values against
     # the written one (FP32 inputs summed in FP64)
@@ -149,7 +153,8 @@ def test_codec_round_trip(codec, u_max, fmt):
     m_out = np.einsum("i,nic->nc", W9, out)
     size = np.einsum("i,nic->nc", W9, np.abs(f64))  # the values' magnitude
     assert np.all(np.abs(m_out - m_in) <= 8 * 2.0 ** -24 * size)
-    # v: the majority's odd axis part where |v_x| + |v_y| <= f^_0, else 0
+    # v: the odd axis part where |v_x| + |v_y| <= f^_0 (majority) or
+    # 4 f^_0 (minority at a wall node), else 0
     vx = np.stack([_half(words[:, W16_VEL] & 0xFFFF, fmt),
                    _half(words[:, W16_VEL] >> 16, fmt)], 1)
     vy = np.stack([_half(words[:, W16_VEL + 1] & 0xFFFF, fmt),
@@ -157,10 +162,13 @@ def test_codec_round_trip(codec, u_max, fmt):
     ox = 0.5 * (f64[:, 1] - f64[:, 3])
     oy = 0.5 * (f64[:, 2] - f64[:, 4])
     major = np.stack([a_major, ~a_major], 1)
-    small = np.abs(ox) + np.abs(oy) <= f64[:, 0] * (1 - 1e-6)
-    use = major & small
-    assert np.all(vx[~use & ~(np.abs(ox) + np.abs(oy) <= f64[:, 0] * (1 + 1e-6))] == 0)
-    assert np.all(vx[~major] == 0) and np.all(vy[~major] == 0)
+    lim = np.where(major, 1.0, 4.0 if wall else 0.0) * f64[:, 0]
+    odd = np.abs(ox) + np.abs(oy)
+    use = odd <= lim * (1 - 1e-6)
+    outside = odd > lim * (1 + 1e-6)
+    assert np.all(vx[outside] == 0) and np.all(vy[outside] == 0)
+    if wall:
+        assert use[~major].mean() > 0.5  # the minority takes v here
     rt = 2.0 ** -FORMATS[fmt][0]
     np.testing.assert_allclose(vx[use], ox[use], rtol=rt, atol=2.0 ** -24)
     np.testing.assert_allclose(vy[use], oy[use], rtol=rt, atol=2.0 ** -24)
