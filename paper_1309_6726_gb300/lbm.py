@@ -140,12 +140,28 @@ _PARAM_KEYS = ("tau_a", "tau_b", "tau_d", "g_coh", "g_ads", "k_r",
                "m_threshold", "c_in", "body_force_x")
 
 
-def _params(p, precision: int) -> Params:
+def _param_values(p) -> tuple:
+    """The model constants of one lattice and its inlet flag, in Params
+    order (p: a dict or an object with those attributes)."""
     if isinstance(p, dict):
-        vals = [p[k] for k in _PARAM_KEYS] + [int(p["inlet"])]
-    else:
-        vals = [getattr(p, k) for k in _PARAM_KEYS] + [int(p.inlet)]
-    return Params(*vals, int(precision))
+        return tuple(float(p[k]) for k in _PARAM_KEYS) + (int(p["inlet"]),)
+    return tuple(float(getattr(p, k)) for k in _PARAM_KEYS) + (int(p.inlet),)
+
+
+def _params(p, precision: int) -> Params:
+    return Params(*_param_values(p), int(precision))
+
+
+#: Geometry and Params as numpy records (the same bytes)
+GEOM_DTYPE = np.dtype([("nx", np.int32), ("ny", np.int32), ("solid", np.uintp),
+                       ("rho_a", np.uintp), ("rho_b", np.uintp),
+                       ("conc", np.uintp), ("cap_x0", np.int32),
+                       ("cap_x1", np.int32)], align=True)
+PARAMS_DTYPE = np.dtype([(k, np.float64) for k in _PARAM_KEYS]
+                        + [("inlet", np.int32), ("precision", np.int32)],
+                        align=True)
+assert GEOM_DTYPE.itemsize == C.sizeof(Geometry)
+assert PARAMS_DTYPE.itemsize == C.sizeof(Params)
 
 
 class Solver:
@@ -167,9 +183,8 @@ class Solver:
         prec = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}[precision]
         self.precision = precision
         self._keep = []
-        G = (Geometry * len(geoms))()
-        P = (Params * len(geoms))()
         self.shapes = []
+        grows, prows = [], []
         for k, (g, p) in enumerate(zip(geoms, params)):
             solid = np.ascontiguousarray(g.solid, dtype=np.uint8)
             if solid.ndim != 2:
@@ -184,13 +199,19 @@ class Solver:
                     raise ValueError("lattice %d: %s has shape %s, solid %s"
                                      % (k, name, a.shape, solid.shape))
             self._keep += [solid, ra, rb, cc]
-            G[k] = Geometry(nx, ny, solid.ctypes.data, ra.ctypes.data,
-                            rb.ctypes.data, cc.ctypes.data, int(g.cap_x0),
-                            int(g.cap_x1))
-            P[k] = _params(p, prec)
+            grows.append((nx, ny, solid.ctypes.data, ra.ctypes.data,
+                          rb.ctypes.data, cc.ctypes.data, int(g.cap_x0),
+                          int(g.cap_x1)))
+            prows.append(_param_values(p) + (int(prec),))
             self.shapes.append((ny, nx))
+        # both struct arrays built in one call each (the same bytes as
+        # arrays of Geometry / Params)
+        G = np.array(grows, GEOM_DTYPE)
+        P = np.array(prows, PARAMS_DTYPE)
         h = C.c_void_p()
-        st = self._lib.lbm_create_batch(G, P, len(geoms), C.byref(h))
+        st = self._lib.lbm_create_batch(G.ctypes.data_as(C.POINTER(Geometry)),
+                                        P.ctypes.data_as(C.POINTER(Params)),
+                                        len(geoms), C.byref(h))
         self._keep = []
         if st != LBM_OK:
             raise LbmError(st, self._lib.lbm_last_error(None).decode())
